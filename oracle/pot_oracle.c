@@ -311,14 +311,19 @@ otree *oracle_build_dense(int depth, const float lo[3], float size, int sh_degre
 
 /* --- point -> voxel ------------------------------------------------------ */
 
-/* Index of the voxel containing coordinate p on one axis; a point on a face
- * goes to the side the ray is heading (dir < 0 -> lower voxel). */
+/* Index of the voxel containing coordinate p on one axis: the k with
+ * lo + k h <= p < lo + (k+1) h; a point on a face goes to the side the ray is
+ * heading (dir < 0 -> lower voxel).  The quotient (p - lo) / h only proposes
+ * k (it can round across a face when p is within ~1e-16 of it, e.g. a tiny p
+ * next to a face at 0); the decision compares p with the face positions
+ * lo + k h, which are exact in fp64 for fp32 lo and size (both sides of the
+ * comparison are exact, so the comparison is). */
 static int64_t voxel_coord(double p, double lo, double h, double dir)
 {
-    double u = (p - lo) / h;
-    double f = floor(u);
-    int64_t q = (int64_t)f;
-    if (u == f && dir < 0) q -= 1;
+    int64_t q = (int64_t)floor((p - lo) / h);
+    for (int it = 0; it < 4 && p < lo + (double)q * h; ++it) --q;
+    for (int it = 0; it < 4 && p >= lo + (double)(q + 1) * h; ++it) ++q;
+    if (dir < 0 && p == lo + (double)q * h) q -= 1;
     return q;
 }
 

@@ -139,7 +139,10 @@ def test_query_exact_membership(oracle_mod, lo, size, D):
     mix = pts[:600].copy()
     sel = rng.integers(0, 2, size=(600, 3)).astype(bool)
     mix[sel] = face[sel]
-    pts = np.concatenate([pts, face, mix]).astype(np.float32)
+    # one ulp below / above faces (includes subnormals next to a face at 0)
+    nxt = np.nextafter(face, np.float32(np.inf)).astype(np.float32)
+    prv = np.nextafter(face, np.float32(-np.inf)).astype(np.float32)
+    pts = np.concatenate([pts, face, mix, nxt, prv]).astype(np.float32)
     got = oracle_mod.query(t, pts)
     for i in range(pts.shape[0]):
         q = [_exact_voxel(pts[i, a], np.float32(lo[a]), np.float32(size), D) for a in range(3)]
