@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Benchmark of the PlenOctree per-ray render path on GB300.
+
+One step = ``pot_render`` of the main workload: a depth-9 octree (512^3
+effective grid) over [-1.5, 1.5]^3 holding ~4.05 M leaves with SH degree 3,
+rendered from 200 orbit cameras of 800 x 800 (128 M rays), early stop at
+T < 1e-4 (the configuration the paper's synthetic-scene FPS is quoted on,
+Sec. 4.1 / Table 1, with synthetic content).
+
+Prints one JSON line (rank 0).  ``value`` is whole-job Mrays/s with the tree
+resident in HBM; ``e2e`` is the same metric through the C ABI with the cameras
+and the output image in host memory (copies inside the timed region).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s @800^2 SH-3 (200 views, depth-9 octree, gamma 1e-4)"
+UNIT = "Mrays/s"
+N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
+
+# DRAM bytes per render launch from the committed ncu capture (see
+# profiles/); reported only while the kernel sources still hash to ``sha``.
+NCU_TRAFFIC = {}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2103_14024_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rays(cams, views, every):
+    """Pixel indices of a bounded sample: every ``every``-th pixel of ``views``."""
+    import numpy as np
+    ci, px, py = [], [], []
+    for v in views:
+        idx = np.arange(0, W * H, every)
+        ci.append(np.full(idx.shape, v))
+        px.append(idx % W)
+        py.append(idx // W)
+    return np.concatenate(ci), np.concatenate(px), np.concatenate(py)
+
+
+def run_oracle_timing(scene, cams, views, every, steps=1):
+    """Times the oracle (as it stands) on the bounded sample; returns (rays/s, rays, seconds, threads)."""
+    from oracle import oracle
+    ot = oracle.build_sparse(scene)
+    ci, px, py = oracle_sample_rays(cams, views, every)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.render_pixels(ot, cams, ci, px, py, gamma=GAMMA)
+    dt = time.perf_counter() - t0
+    return ci.shape[0] * steps / dt, ci.shape[0], dt, oracle.num_threads()
+
+
+def reference_arm(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2103_14024_gb300 import synth
+    scene = synth.scene_shapes()
+    cams = synth.cameras_main(N_VIEWS, W, H)
+    views = [0]
+    every = 1
+    for _ in range(args.warmup):
+        run_oracle_timing(scene, cams, views, every)
+    rate, n, dt, thr = run_oracle_timing(scene, cams, views, every, steps=args.steps)
+    value = rate / 1e6
+    sample = f"{n} rays per step (all pixels of view 0 of 200), {args.steps} steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(scene, "f32"),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(scene, dtype):
+    return {"workload": "main plain render: depth-9 octree (512^3) over [-1.5,1.5]^3, union of 8 seeded "
+                        "spheres/boxes, SH degree 3, 200 orbit views of 800x800, gamma 1e-4",
+            "leaves": int(scene.n), "views": N_VIEWS, "width": W, "height": H, "rays_per_step": N_VIEWS * W * H,
+            "sh_degree": 3, "leaf_dtype": dtype, "gamma": GAMMA,
+            "l2": "no flush: inputs and outputs larger than L2 (tree >= 0.4 GB read, 1.54 GB of rgb written per step)"}
+
+
+def algorithmic_bytes(pot, torch, tree, cams, dtype, leaf_bytes):
+    """Per-launch algorithmic bytes: sum over views of (distinct leaves composited in the view) x leaf
+    record bytes (the HBM floor), plus the rgb output; also the touched bytes (every composited leaf
+    segment) for the L2 view.  Counted with the library's counting launch, outside the timed region."""
+    n_leaves = tree.info()["n_leaves"]
+    touched = torch.zeros(n_leaves, dtype=torch.uint8, device="cuda")
+    seg = torch.zeros((1, H, W), dtype=torch.int32, device="cuda")
+    rgb = torch.empty((1, H, W, 3), dtype=torch.float32, device="cuda")
+    uniq, segs = 0, 0
+    for v in range(len(cams)):
+        touched.zero_()
+        pot.render(tree, cams[v:v + 1], rgb=rgb, gamma=GAMMA, seg_count=seg, leaf_touched=touched)
+        uniq += int(touched.sum().item())
+        segs += int(seg.sum().item())
+    rays = len(cams) * W * H
+    out_bytes = 12 * rays
+    return {"unique_leaves": uniq, "leaf_segments": segs, "hbm_bytes": uniq * leaf_bytes + out_bytes,
+            "touched_bytes": segs * leaf_bytes + out_bytes, "rays": rays}
+
+
+def l2_read_peak(torch):
+    """Rough L2 bandwidth: repeated copy of a 24 MB buffer (read + write bytes)."""
+    x = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device="cuda").uniform_()
+    y = torch.empty_like(x)
+    for _ in range(20):
+        y.copy_(x)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 400
+    s.record()
+    for _ in range(n):
+        y.copy_(x)
+    e.record()
+    torch.cuda.synchronize()
+    return 2 * x.numel() * 4 * n / (s.elapsed_time(e) * 1e-3) / 1e9
+
+
+def time_steps(torch, fn, steps, warmup, barrier):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = time.perf_counter()
+    for s, e in evs:
+        s.record()
+        fn()
+        e.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    per = [s.elapsed_time(e) for s, e in evs]
+    return wall, per
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--variants", default="f16,bf16", help="extra leaf dtypes to time ('' for none)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+    import paper_2103_14024_gb300 as pot
+    from paper_2103_14024_gb300 import synth
+
+    rank, local, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    scene = synth.scene_shapes()
+    cams = synth.cameras_main(N_VIEWS, W, H)
+    ccams = pot.make_cameras(cams)
+    rays = N_VIEWS * W * H
+
+    def measure(dtype, e2e=False):
+        tree = pot.Tree.from_scene(scene, dtype=dtype)
+        info = tree.info()
+        rgb = torch.empty((N_VIEWS, H, W, 3), dtype=torch.float32, device="cuda")
+
+        def step():
+            pot.render(tree, ccams, rgb=rgb, gamma=GAMMA)
+
+        l0 = pot.launch_count()
+        with ClockSampler(dev_index) as clk:
+            wall, per = time_steps(torch, step, args.steps, args.warmup, barrier)
+        launches = (pot.launch_count() - l0)
+        launches_timed = launches * args.steps // (args.steps + args.warmup)
+        pot.check()
+        res = {"tree": tree, "info": info, "wall": wall, "per": per, "clk": clk.summary(),
+               "launches": launches_timed}
+        if e2e:
+            host = torch.empty((N_VIEWS, H, W, 3), dtype=torch.float32, pin_memory=True)
+
+            def step_e2e():
+                pot.render(tree, ccams, rgb=host, gamma=GAMMA)   # host output: D2H + sync inside
+
+            wall_e, _ = time_steps(torch, step_e2e, max(3, args.steps // 2), 1, barrier)
+            res["e2e_wall"] = wall_e / max(3, args.steps // 2)
+            del host
+        return res
+
+    main_res = measure(args.dtype, e2e=not args.no_e2e)
+    leaf_bytes = int(main_res["info"]["leaf_bytes"])
+    alg = algorithmic_bytes(pot, torch, main_res["tree"], ccams, args.dtype, leaf_bytes)
+
+    # whole-job time: max over ranks of the timed region
+    wall = main_res["wall"]
+    if dist is not None:
+        t = torch.tensor([wall], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t.item())
+    ms_per_step = 1e3 * wall / args.steps
+    value = world * rays / (wall / args.steps) / 1e6
+    avg_launch_ms = sum(main_res["per"]) / len(main_res["per"])
+    peak, peak_kind = measured_peaks()
+    achieved = alg["hbm_bytes"] / (avg_launch_ms * 1e-3) / 1e9
+    sha = kernel_sha()
+    traffic = None
+    if NCU_TRAFFIC.get(args.dtype, {}).get("sha") == sha:
+        traffic = NCU_TRAFFIC[args.dtype]["bytes_per_launch"]
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": workload_config(scene, args.dtype),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "peak_source": f"hbm_gbs of {peak_kind}",
+                     "algorithmic_bytes_per_launch": alg["hbm_bytes"],
+                     "kernel": "render_kernel<16,float,cams>", "avg_launch_ms": round(avg_launch_ms, 3)},
+        "gpu_launches": int(main_res["launches"]),
+        "clocks": main_res["clk"],
+    }
+    if rank == 0:
+        try:
+            l2p = l2_read_peak(torch)
+            line["l2"] = {"achieved": round(alg["touched_bytes"] / (avg_launch_ms * 1e-3) / 1e9, 1),
+                          "peak": round(l2p, 1), "unit": "GB/s", "peak_source": "24 MB device copy loop (measured here)",
+                          "touched_bytes_per_launch": alg["touched_bytes"],
+                          "frac": round(alg["touched_bytes"] / (avg_launch_ms * 1e-3) / 1e9 / l2p, 4)}
+        except Exception as e:  # noqa: BLE001
+            line["l2"] = {"error": str(e)}
+        line["counts"] = {"unique_leaves_summed_over_views": alg["unique_leaves"],
+                          "leaf_segments": alg["leaf_segments"],
+                          "mean_leaf_segments_per_ray": round(alg["leaf_segments"] / rays, 3)}
+    if not args.no_e2e:
+        e2e_value = world * rays / main_res["e2e_wall"] / 1e6
+        line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * N_VIEWS,
+                       "d2h_bytes_per_step": 12 * rays}
+    variants = {}
+    for vd in [v for v in args.variants.split(",") if v and v != args.dtype]:
+        r = measure(vd)
+        w = r["wall"]
+        vb = algorithmic_bytes(pot, torch, r["tree"], ccams, vd, int(r["info"]["leaf_bytes"]))
+        avg = sum(r["per"]) / len(r["per"])
+        variants[vd] = {"value": round(world * rays / (w / args.steps) / 1e6, 3),
+                        "ms_per_step": round(1e3 * w / args.steps, 3),
+                        "roofline": {"bound": "hbm", "achieved": round(vb["hbm_bytes"] / (avg * 1e-3) / 1e9, 1),
+                                     "peak": peak, "unit": "GB/s",
+                                     "frac": round(vb["hbm_bytes"] / (avg * 1e-3) / 1e9 / peak, 4),
+                                     "traffic": (NCU_TRAFFIC.get(vd, {}).get("bytes_per_launch")
+                                                 if NCU_TRAFFIC.get(vd, {}).get("sha") == sha else None)},
+                        "clocks": r["clk"], "leaf_bytes": int(r["info"]["leaf_bytes"])}
+        r["tree"].free()
+    if variants:
+        line["variants"] = variants
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        views = [0, 25, 50, 75, 100, 125, 150, 175]
+        rate, n, dt, thr = run_oracle_timing(scene, cams, views, 2)
+        line["cpu_baseline"] = {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
+                                "sample": f"every 2nd pixel of views 0,25,...,175 ({n} rays, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * pot.h -- C ABI of the GB300 PlenOctree renderer (libpot.so).
+ *
+ * Method: PlenOctrees for Real-time Rendering of Neural Radiance Fields
+ * (Yu, Li, Tancik, Li, Ng, Kanazawa; ICCV 2021).  A sparse octree stores, in
+ * every leaf at the deepest level, a density sigma and real spherical-harmonic
+ * coefficients k_l^m in R^3 (Sec. 3.1, Sec. 3.2).  A pixel is rendered by
+ * cutting its ray at the voxel boundaries of the octree into segments of
+ * constant density and colour, colouring each leaf with the sigmoid of its SH
+ * expansion at the ray direction, and compositing with the NeRF quadrature
+ * (Eq. 1) plus a background term (App. B.3.2), stopping early once the
+ * transmittance falls below gamma (Sec. 3.2 "Rendering").
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: depth D (1..12), R = 2^D voxels per axis over the cube
+ *     [bbox_lo, bbox_lo + bbox_size)^3; voxel k on an axis is the half-open
+ *     interval [lo + k h, lo + (k+1) h), h = bbox_size / 2^D (exact).
+ *   - Morton code of voxel (x,y,z): bits interleaved with x most significant
+ *     in each triple, m = sum_b x_b<<(3b+2) | y_b<<(3b+1) | z_b<<3b.
+ *   - Canonical tree arrays (pot_tree_export): nodes in breadth-first order
+ *     (root = 0; each level by ascending Morton prefix); child[n][s] with slot
+ *     s = (x_bit<<2)|(y_bit<<1)|z_bit of the node's level, value 0 = empty,
+ *     > 0 node index, < 0 -(leaf+1); leaves numbered by ascending Morton code.
+ *   - SH: K = (sh_degree+1)^2 coefficients per channel, index k = l^2 + l + m,
+ *     RGB innermost ([K][3]); real basis from the complex Y_l^m with the
+ *     Condon-Shortley phase (App. B.1), theta from +z, phi = atan2(y, x),
+ *     evaluated at the unit ray direction.  Degree 1 is (+y, +z, +x) * sqrt(3/4pi).
+ *   - Distances (near, far, segment length delta) are world units along the ray.
+ *   - Pixel ray of a pinhole camera (column i, row j), fp32 in this order, each
+ *     operation IEEE round-to-nearest, no contraction:
+ *       xc = ((float)i + 0.5 - cx) / fx;  yc = -(((float)j + 0.5 - cy) / fy)
+ *       d_r = (c2w[r][0]*xc + c2w[r][1]*yc) - c2w[r][2];   o_r = c2w[r][3]
+ *     (camera looks along its -z axis; the direction need not be unit length).
+ *
+ * Memory and streams.  Every call is asynchronous on the caller's stream
+ * unless stated otherwise; a NULL stream is the legacy default stream.  Array
+ * arguments may live in host or device memory where a function says so (the
+ * library detects which); when an output is in host memory the call
+ * synchronises the stream before returning.  Inputs are read-only and owned by
+ * the caller; trees are owned by the library and released by pot_tree_free.
+ *
+ * Errors.  Every entry point returns a pot_status; POT_OK is 0.  The message
+ * of the last failure on the calling thread is returned by pot_last_error().
+ * A render whose traversal exceeds its step bound (3 * 2^D + 16 cells per
+ * ray, never expected for a well formed tree) stops that ray and raises a
+ * device error word, which pot_check() reports as POT_ERR_TRAVERSAL.
+ */
+#ifndef POT_H
+#define POT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *pot_stream;
+
+typedef enum pot_status {
+    POT_OK = 0,
+    POT_ERR_INVALID_ARG = 1,
+    POT_ERR_OOM = 2,
+    POT_ERR_CUDA = 3,
+    POT_ERR_TRAVERSAL = 4,
+    POT_ERR_BUDGET = 5,
+    POT_ERR_UNSUPPORTED = 6
+} pot_status;
+
+/* Storage type of leaf values (density and SH).  Arithmetic is fp32 always;
+ * the paper optimises in float32 and stores the tree in float16 (App. C,
+ * PlenOctree optimisation details). */
+typedef enum pot_dtype { POT_F32 = 0, POT_F16 = 1, POT_BF16 = 2 } pot_dtype;
+
+typedef struct pot_tree pot_tree;
+
+typedef struct pot_build_desc {
+    int32_t depth;         /* D, 1..12 (1..10 for pot_build from a dense grid) */
+    int32_t sh_degree;     /* 0..3 */
+    int32_t leaf_dtype;    /* pot_dtype */
+    float sigma_threshold; /* pot_build keeps voxel iff sigma > threshold */
+    float bbox_lo[3];
+    float bbox_size;       /* > 0 */
+} pot_build_desc;
+
+/* 80 bytes.  c2w: rows of the camera-to-world matrix; columns are the camera
+ * right, up and back (= -viewing direction) axes and the eye position. */
+typedef struct pot_camera {
+    float c2w[3][4];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near, far;
+} pot_camera;
+
+typedef struct pot_render_opts {
+    float bg[3];      /* background colour c_N (App. B.3.2); default 0 */
+    float gamma;      /* early stop when transmittance < gamma; 0 disables */
+    float near, far;  /* pot_render_rays only: clip range (world distance) */
+    uint32_t flags;   /* reserved, must be 0 */
+    int32_t max_steps; /* cells visited per ray before the ray is stopped and the
+                          device error word raised; 0 = 3 * 2^D + 16, which no
+                          ray of a well formed tree can reach */
+    /* Optional device outputs for measurement (NULL to skip):
+     *   seg_count[ray]   number of leaf segments composited
+     *   leaf_touched[L]  set to 1 for every leaf composited by some ray   */
+    int32_t *seg_count;
+    uint8_t *leaf_touched;
+} pot_render_opts;
+
+typedef struct pot_tree_info {
+    int32_t depth, sh_degree, sh_dim, leaf_dtype;
+    int64_t n_nodes, n_leaves;
+    int64_t bytes;        /* device bytes held by the tree */
+    int64_t leaf_bytes;   /* bytes of one leaf record as stored (sigma + SH, padding included) */
+    float bbox_lo[3];
+    float bbox_size;
+    int32_t saturated;    /* 1 if some value overflowed fp16/bf16 and was clamped */
+    int32_t device;
+} pot_tree_info;
+
+/* ---------------------------------------------------------------- build ---
+ * Sec. 3.2 "Filtering": the kept voxels become leaves at the deepest level
+ * and the tree is empty elsewhere.  A node exists iff it has a kept
+ * descendant; leaf values are copied (rounded to nearest even and saturated
+ * for fp16 / bf16 storage).
+ *
+ * pot_build: dense grids, host or device memory, indexed [x][y][z]:
+ *   sigma [R][R][R] float32, sh [R][R][R][K][3] float32.
+ *   A voxel is kept iff sigma > desc->sigma_threshold.  A NaN or infinite
+ *   sigma gives POT_ERR_INVALID_ARG.
+ * pot_build_sparse: n kept voxels, host or device memory:
+ *   morton [n] uint64 strictly increasing and < 8^D (else
+ *   POT_ERR_INVALID_ARG), sigma [n] float32 (finite), sh [n][K][3] float32.
+ * *out receives a new tree on the current device.  Synchronises the stream. */
+pot_status pot_build(const pot_build_desc *desc, const float *sigma, const float *sh, pot_tree **out,
+                     pot_stream stream);
+pot_status pot_build_sparse(const pot_build_desc *desc, int64_t n, const uint64_t *morton,
+                            const float *sigma, const float *sh, pot_tree **out, pot_stream stream);
+
+pot_status pot_tree_get_info(const pot_tree *tree, pot_tree_info *info);
+
+/* Canonical arrays (conventions above) into caller buffers in host or device
+ * memory: child [n_nodes][8] int32, sigma [n_leaves] float32, sh
+ * [n_leaves][K][3] float32 (stored values widened exactly), morton
+ * [n_leaves] uint64.  Any pointer may be NULL. */
+pot_status pot_tree_export(const pot_tree *tree, int32_t *child, float *sigma, float *sh,
+                           uint64_t *morton, pot_stream stream);
+
+/* Overwrites leaf values from caller arrays (same layouts as pot_build_sparse,
+ * host or device memory); the structure is unchanged. */
+pot_status pot_tree_set_values(pot_tree *tree, const float *sigma, const float *sh, pot_stream stream);
+
+/* Synchronises the tree's device and frees it.  NULL is accepted. */
+pot_status pot_tree_free(pot_tree *tree);
+
+/* ---------------------------------------------------------------- query ---
+ * Leaf containing each point xyz [n][3] float32: leaf index >= 0, -1 for
+ * empty space inside the box, -2 outside the box (or NaN).  Exact membership
+ * (conventions above).  xyz and leaf_out in device memory. */
+pot_status pot_query(const pot_tree *tree, int64_t n, const float *xyz, int32_t *leaf_out,
+                     pot_stream stream);
+
+/* Real SH basis Y_k, k < K, at the directions dirs [n][3] (normalised
+ * inside) into Y [n][K] float32; device memory.  App. B.1. */
+pot_status pot_sh_basis(int32_t K, int64_t n, const float *dirs, float *Y, pot_stream stream);
+
+/* --------------------------------------------------------------- render ---
+ * Sec. 3.2 "Rendering", Eq. 1, App. B.3.2: for every pixel of every camera,
+ *   C = sum_i T_i (1 - exp(-max(sigma_i,0) delta_i)) c_i + T_N bg,
+ *   T_i = exp(-sum_{j<i} max(sigma_j,0) delta_j),
+ *   c_i = sigmoid(sum_k k_{i,k} Y_k(d)),
+ * over the leaf segments of the ray clipped to the box and to [near, far];
+ * stops after the first segment that leaves T < gamma.
+ *   cams [n_cams] in host memory, all with the same width and height;
+ *   rgb [n_cams][H][W][3] float32 and t_final [n_cams][H][W] float32 (final
+ *   transmittance T_N; may be NULL), host or device memory.               */
+pot_status pot_render(const pot_tree *tree, const pot_camera *cams, int32_t n_cams,
+                      const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
+
+/* Same for arbitrary rays: origins [n][3], dirs [n][3] (not necessarily unit)
+ * float32; rgb [n][3], t_final [n]; host or device memory.               */
+pot_status pot_render_rays(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
+                           const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
+
+/* Number of CUDA kernels launched by this library in this process since it
+ * was loaded (a counter for benchmarks). */
+int64_t pot_launch_count(void);
+
+/* Synchronises the stream and returns POT_ERR_TRAVERSAL if any render on
+ * this device raised the device error word since the last check (the word
+ * is cleared), POT_ERR_CUDA on a CUDA error, else POT_OK. */
+pot_status pot_check(pot_stream stream);
+
+const char *pot_last_error(void);
+int32_t pot_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POT_H */

@@ -1,0 +1,314 @@
+"""GB300 PlenOctree renderer: Python binding of ``libpot.so``.
+
+Argument marshalling only: every step of the render path runs in the CUDA
+kernels of ``libpot.so`` (sources in ``csrc/``, C ABI in ``include/pot.h``).
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the
+library is missing, every call raises.
+
+Method: PlenOctrees for Real-time Rendering of Neural Radiance Fields
+(Yu et al., ICCV 2021), Sec. 3.2 (octree rendering and conversion), Eq. 1
+(quadrature), App. B.1 (real SH basis), App. B.3 (derivatives).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpot.so")
+
+POT_OK, POT_ERR_INVALID_ARG, POT_ERR_OOM, POT_ERR_CUDA, POT_ERR_TRAVERSAL, POT_ERR_BUDGET, \
+    POT_ERR_UNSUPPORTED = range(7)
+DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+_STATUS = {0: "POT_OK", 1: "POT_ERR_INVALID_ARG", 2: "POT_ERR_OOM", 3: "POT_ERR_CUDA",
+           4: "POT_ERR_TRAVERSAL", 5: "POT_ERR_BUDGET", 6: "POT_ERR_UNSUPPORTED"}
+
+
+class PotError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BuildDesc(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("sh_degree", C.c_int32), ("leaf_dtype", C.c_int32),
+                ("sigma_threshold", C.c_float), ("bbox_lo", C.c_float * 3), ("bbox_size", C.c_float)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("c2w", (C.c_float * 4) * 3), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("near", C.c_float),
+                ("far", C.c_float)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("bg", C.c_float * 3), ("gamma", C.c_float), ("near", C.c_float), ("far", C.c_float),
+                ("flags", C.c_uint32), ("max_steps", C.c_int32), ("seg_count", C.c_void_p),
+                ("leaf_touched", C.c_void_p)]
+
+
+class TreeInfo(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("sh_degree", C.c_int32), ("sh_dim", C.c_int32),
+                ("leaf_dtype", C.c_int32), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
+                ("bytes", C.c_int64), ("leaf_bytes", C.c_int64), ("bbox_lo", C.c_float * 3),
+                ("bbox_size", C.c_float), ("saturated", C.c_int32), ("device", C.c_int32)]
+
+
+assert C.sizeof(Camera) == 80
+
+_lib = None
+_lock = threading.Lock()
+
+_p = C.c_void_p
+_SIGS = {
+    "pot_build": [_p, _p, _p, _p, _p],
+    "pot_build_sparse": [_p, C.c_int64, _p, _p, _p, _p, _p],
+    "pot_tree_get_info": [_p, _p],
+    "pot_tree_export": [_p, _p, _p, _p, _p, _p],
+    "pot_tree_set_values": [_p, _p, _p, _p],
+    "pot_tree_free": [_p],
+    "pot_query": [_p, C.c_int64, _p, _p, _p],
+    "pot_sh_basis": [C.c_int32, C.c_int64, _p, _p, _p],
+    "pot_render": [_p, _p, C.c_int32, _p, _p, _p, _p],
+    "pot_render_rays": [_p, C.c_int64, _p, _p, _p, _p, _p, _p],
+    "pot_check": [_p],
+}
+
+
+def lib():
+    """The loaded ``libpot.so`` (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.pot_last_error.restype = C.c_char_p
+            L.pot_last_error.argtypes = []
+            L.pot_version.restype = C.c_int32
+            L.pot_launch_count.restype = C.c_int64
+            _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != POT_OK:
+        raise PotError(st, lib().pot_last_error().decode(errors="replace"))
+
+
+def last_error() -> str:
+    return lib().pot_last_error().decode(errors="replace")
+
+
+def launch_count() -> int:
+    return int(lib().pot_launch_count())
+
+
+# ----------------------------------------------------------------------------
+# pointers: torch tensors (any device) or numpy arrays (host)
+# ----------------------------------------------------------------------------
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    # torch.Tensor
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(x.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _as_np(x, dtype):
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def make_cameras(cams_np) -> C.Array:
+    """ctypes array of Camera from a numpy structured array with the synth.CAMERA_DTYPE layout."""
+    cams_np = np.ascontiguousarray(cams_np)
+    arr = (Camera * len(cams_np))()
+    C.memmove(arr, cams_np.ctypes.data, 80 * len(cams_np))
+    return arr
+
+
+def _opts(bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0, far=3.0e38, seg_count=None, leaf_touched=None,
+          max_steps=0):
+    o = RenderOpts()
+    o.max_steps = max_steps
+    o.bg[0], o.bg[1], o.bg[2] = bg
+    o.gamma = gamma
+    o.near = near
+    o.far = far
+    o.flags = 0
+    o.seg_count = None if seg_count is None else seg_count.data_ptr()
+    o.leaf_touched = None if leaf_touched is None else leaf_touched.data_ptr()
+    return o
+
+
+# ----------------------------------------------------------------------------
+# trees
+# ----------------------------------------------------------------------------
+
+class Tree:
+    """A PlenOctree resident on the GPU (owned by libpot)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            lib().pot_tree_free(h)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("tree was freed")
+        return self._h
+
+    @staticmethod
+    def _desc(depth, sh_degree, dtype, bbox_lo, bbox_size, threshold=0.0):
+        d = BuildDesc()
+        d.depth, d.sh_degree, d.leaf_dtype = depth, sh_degree, DTYPES[dtype]
+        d.sigma_threshold = threshold
+        for a in range(3):
+            d.bbox_lo[a] = bbox_lo[a]
+        d.bbox_size = bbox_size
+        return d
+
+    @classmethod
+    def build_sparse(cls, depth, sh_degree, bbox_lo, bbox_size, morton, sigma, sh, dtype="f32",
+                     stream=None) -> "Tree":
+        """``pot_build_sparse``; arrays are numpy (host) or torch tensors (any device)."""
+        d = cls._desc(depth, sh_degree, dtype, bbox_lo, bbox_size)
+        if isinstance(morton, np.ndarray):
+            morton = _as_np(morton, np.uint64)
+            sigma = _as_np(sigma, np.float32)
+            sh = _as_np(sh, np.float32)
+        n = int(morton.shape[0])
+        out = C.c_void_p()
+        _check(lib().pot_build_sparse(C.byref(d), n, _ptr(morton), _ptr(sigma), _ptr(sh), C.byref(out),
+                                      _stream(stream)))
+        return cls(out.value)
+
+    @classmethod
+    def from_scene(cls, scene, dtype="f32", stream=None) -> "Tree":
+        return cls.build_sparse(scene.depth, scene.sh_degree, scene.bbox_lo, scene.bbox_size,
+                                scene.morton, scene.sigma, scene.sh, dtype=dtype, stream=stream)
+
+    @classmethod
+    def build_dense(cls, depth, sh_degree, bbox_lo, bbox_size, sigma, sh, threshold=0.0, dtype="f32",
+                    stream=None) -> "Tree":
+        """``pot_build`` from dense grids sigma [R,R,R], sh [R,R,R,K,3] indexed [x][y][z]."""
+        d = cls._desc(depth, sh_degree, dtype, bbox_lo, bbox_size, threshold)
+        if isinstance(sigma, np.ndarray):
+            sigma = _as_np(sigma, np.float32)
+            sh = _as_np(sh, np.float32)
+        out = C.c_void_p()
+        _check(lib().pot_build(C.byref(d), _ptr(sigma), _ptr(sh), C.byref(out), _stream(stream)))
+        return cls(out.value)
+
+    def info(self) -> dict:
+        i = TreeInfo()
+        _check(lib().pot_tree_get_info(self.handle, C.byref(i)))
+        return {f: (list(getattr(i, f)) if f == "bbox_lo" else getattr(i, f)) for f, _ in TreeInfo._fields_}
+
+    def export(self, stream=None):
+        """Canonical arrays (numpy): child [N,8] int32, sigma [L] f32, sh [L,K,3] f32, morton [L] u64."""
+        inf = self.info()
+        N, L, K = inf["n_nodes"], inf["n_leaves"], inf["sh_dim"]
+        child = np.zeros((N, 8), np.int32)
+        sigma = np.zeros(L, np.float32)
+        sh = np.zeros((L, K, 3), np.float32)
+        morton = np.zeros(L, np.uint64)
+        _check(lib().pot_tree_export(self.handle, _ptr(child), _ptr(sigma), _ptr(sh), _ptr(morton),
+                                     _stream(stream)))
+        return child, sigma, sh, morton
+
+    def set_values(self, sigma, sh, stream=None):
+        _check(lib().pot_tree_set_values(self.handle, _ptr(sigma), _ptr(sh), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# calls
+# ----------------------------------------------------------------------------
+
+def query(tree: Tree, xyz, out=None, stream=None):
+    """``pot_query``: leaf index per point (torch int32 tensor on the points' device)."""
+    import torch
+    n = int(xyz.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    _check(lib().pot_query(tree.handle, n, _ptr(xyz), _ptr(out), _stream(stream)))
+    return out
+
+
+def sh_basis(K: int, dirs, out=None, stream=None):
+    import torch
+    n = int(dirs.shape[0])
+    if out is None:
+        out = torch.empty((n, K), dtype=torch.float32, device=dirs.device)
+    _check(lib().pot_sh_basis(K, n, _ptr(dirs), _ptr(out), _stream(stream)))
+    return out
+
+
+def render(tree: Tree, cams, rgb=None, t_final=None, bg=(0.0, 0.0, 0.0), gamma=0.0, want_t_final=False,
+           seg_count=None, leaf_touched=None, max_steps=0, device="cuda", stream=None):
+    """``pot_render``: rgb [n_cams, H, W, 3] float32 (torch, on ``device`` unless given)."""
+    import torch
+    carr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    n = len(carr)
+    H, W = (carr[0].height, carr[0].width) if n else (0, 0)
+    if rgb is None:
+        rgb = torch.empty((n, H, W, 3), dtype=torch.float32, device=device)
+    if want_t_final and t_final is None:
+        t_final = torch.empty((n, H, W), dtype=torch.float32, device=rgb.device if hasattr(rgb, "device") else device)
+    o = _opts(bg, gamma, seg_count=seg_count, leaf_touched=leaf_touched, max_steps=max_steps)
+    _check(lib().pot_render(tree.handle, carr, n, C.byref(o), _ptr(rgb), _ptr(t_final), _stream(stream)))
+    return (rgb, t_final) if want_t_final else rgb
+
+
+def render_rays(tree: Tree, origins, dirs, rgb=None, t_final=None, bg=(0.0, 0.0, 0.0), gamma=0.0,
+                near=0.0, far=3.0e38, want_t_final=False, seg_count=None, leaf_touched=None, max_steps=0,
+                stream=None):
+    """``pot_render_rays``: rgb [n, 3] float32 on the rays' device."""
+    import torch
+    n = int(origins.shape[0])
+    dev = origins.device if hasattr(origins, "device") else "cpu"
+    if rgb is None:
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    if want_t_final and t_final is None:
+        t_final = torch.empty(n, dtype=torch.float32, device=dev)
+    o = _opts(bg, gamma, near, far, seg_count=seg_count, leaf_touched=leaf_touched, max_steps=max_steps)
+    _check(lib().pot_render_rays(tree.handle, n, _ptr(origins), _ptr(dirs), C.byref(o), _ptr(rgb),
+                                 _ptr(t_final), _stream(stream)))
+    return (rgb, t_final) if want_t_final else rgb
+
+
+def check(stream=None):
+    """``pot_check``: synchronise and raise on a device-side traversal error."""
+    _check(lib().pot_check(_stream(stream)))

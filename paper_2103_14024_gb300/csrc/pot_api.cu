@@ -1,0 +1,580 @@
+// pot_api.cu -- the C ABI of libpot.so: argument checks, host/device staging,
+// error reporting, tree lifetime, and the launches.  Every numeric step runs in
+// the kernels of pot_build.cu, pot_query.cu and pot_render_*.cu.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "pot_device.cuh"
+#include "pot_internal.h"
+
+namespace pot {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Raised (bit 0) by a render whose traversal hit its step bound.
+__device__ unsigned int g_error_word;
+
+unsigned int *device_error_word()
+{
+    static std::mutex mu;
+    static unsigned int *ptr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<unsigned int *>(p);
+    }
+    return ptr[dev];
+}
+
+}  // namespace pot
+
+using namespace pot;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+pot_status fail(pot_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pot_status cuda_fail(cudaError_t e, const char *where)
+{
+    cudaGetLastError();  // clear a sticky launch error of this thread
+    return fail(e == cudaErrorMemoryAllocation ? POT_ERR_OOM : POT_ERR_CUDA, "%s: %s (%d)", where,
+                cudaGetErrorString(e), (int)e);
+}
+
+#define POT_CUDA(call, where)                              \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered temporary device buffer.
+struct Tmp {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Tmp()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+    cudaError_t alloc(size_t bytes, cudaStream_t st)
+    {
+        s = st;
+        return cudaMallocAsync(&p, bytes > 0 ? bytes : 16, st);
+    }
+};
+
+// A device view of an input array that may live in host memory.
+cudaError_t stage_in(const void *src, size_t bytes, Tmp &tmp, cudaStream_t s, const void **out)
+{
+    if (!src || is_device_ptr(src)) {
+        *out = src;
+        return cudaSuccess;
+    }
+    cudaError_t e = tmp.alloc(bytes, s);
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(tmp.p, src, bytes, cudaMemcpyHostToDevice, s);
+    *out = tmp.p;
+    return e;
+}
+
+// A device destination for an output that may live in host memory; finish()
+// copies back and synchronises when needed.
+struct Out {
+    void *user = nullptr;
+    size_t bytes = 0;
+    Tmp tmp;
+    bool host = false;
+    cudaError_t bind(void *dst, size_t n, cudaStream_t s, void **dev)
+    {
+        user = dst;
+        bytes = n;
+        host = dst && !is_device_ptr(dst);
+        if (!host) {
+            *dev = dst;
+            return cudaSuccess;
+        }
+        cudaError_t e = tmp.alloc(n, s);
+        *dev = tmp.p;
+        return e;
+    }
+    cudaError_t finish(cudaStream_t s)
+    {
+        if (!host || !bytes) return cudaSuccess;
+        return cudaMemcpyAsync(user, tmp.p, bytes, cudaMemcpyDeviceToHost, s);
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int elem_bytes(int dtype) { return dtype == POT_F32 ? 4 : 2; }
+
+int stride_for(int dtype, int K)
+{
+    return dtype == POT_F32 ? sh_stride<float>(K) : sh_stride<__half>(K);
+}
+
+pot_status check_desc(const pot_build_desc *d, int max_depth)
+{
+    if (!d) return fail(POT_ERR_INVALID_ARG, "desc is NULL");
+    if (d->depth < 1 || d->depth > max_depth)
+        return fail(POT_ERR_INVALID_ARG, "depth %d outside 1..%d", d->depth, max_depth);
+    if (d->sh_degree < 0 || d->sh_degree > 3)
+        return fail(POT_ERR_INVALID_ARG, "sh_degree %d outside 0..3", d->sh_degree);
+    if (d->leaf_dtype < POT_F32 || d->leaf_dtype > POT_BF16)
+        return fail(POT_ERR_INVALID_ARG, "leaf_dtype %d unknown", d->leaf_dtype);
+    if (!(d->bbox_size > 0.f) || !std::isfinite(d->bbox_size))
+        return fail(POT_ERR_INVALID_ARG, "bbox_size must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d->bbox_lo[a])) return fail(POT_ERR_INVALID_ARG, "bbox_lo must be finite");
+    if (!std::isfinite(d->sigma_threshold)) return fail(POT_ERR_INVALID_ARG, "sigma_threshold not finite");
+    return POT_OK;
+}
+
+pot_tree *new_tree(const pot_build_desc *d, int dev)
+{
+    pot_tree *t = new (std::nothrow) pot_tree();
+    if (!t) return nullptr;
+    t->device = dev;
+    t->desc = *d;
+    t->K = (d->sh_degree + 1) * (d->sh_degree + 1);
+    t->stride = stride_for(d->leaf_dtype, t->K);
+    t->elem_bytes = elem_bytes(d->leaf_dtype);
+    t->h = std::ldexp(d->bbox_size, -d->depth);
+    return t;
+}
+
+void destroy_tree(pot_tree *t)
+{
+    if (!t) return;
+    DeviceGuard g(t->device);
+    cudaDeviceSynchronize();
+    cudaFree(t->child);
+    cudaFree(t->sigma);
+    cudaFree(t->sh);
+    cudaFree(t->morton);
+    delete t;
+}
+
+// Shared tail of both builds: codes, sigma, sh are device arrays of n kept voxels.
+pot_status finish_build(const pot_build_desc *desc, int64_t n, const uint64_t *d_codes,
+                        const float *d_sigma, const float *d_sh, unsigned *d_flags, pot_tree **out,
+                        cudaStream_t s)
+{
+    int dev = 0;
+    POT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    pot_tree *t = new_tree(desc, dev);
+    if (!t) return fail(POT_ERR_OOM, "host allocation failed");
+    t->n_leaves = n;
+    cudaError_t e = cudaMalloc(&t->morton, sizeof(uint64_t) * (n > 0 ? n : 1));
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(t->morton, d_codes, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+    int status = 0;
+    if (e == cudaSuccess) e = build_levels_and_children(t, n, d_codes, s, d_flags, &status);
+    if (e == cudaSuccess && status == 0) e = pack_leaves(t, d_sigma, d_sh, d_flags, s);
+    unsigned flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        destroy_tree(t);
+        return cuda_fail(e, "pot_build");
+    }
+    if (status != 0) {
+        destroy_tree(t);
+        return fail(POT_ERR_UNSUPPORTED, "tree too large (%d)", status);
+    }
+    t->saturated = (flags & 4u) ? 1 : 0;
+    t->bytes = t->n_nodes * 32 + n * 8 + ((n * t->elem_bytes + 255) / 256) * 256 +
+               n * (int64_t)t->stride * t->elem_bytes;
+    *out = t;
+    return POT_OK;
+}
+
+pot_status check_opts(const pot_render_opts *o)
+{
+    if (!o) return POT_OK;
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(o->bg[c])) return fail(POT_ERR_INVALID_ARG, "bg must be finite");
+    if (!(o->gamma >= 0.f) || !std::isfinite(o->gamma))
+        return fail(POT_ERR_INVALID_ARG, "gamma must be finite and >= 0");
+    if (o->flags != 0) return fail(POT_ERR_INVALID_ARG, "opts.flags must be 0");
+    if (o->max_steps < 0) return fail(POT_ERR_INVALID_ARG, "max_steps < 0");
+    if ((o->seg_count == nullptr) != (o->leaf_touched == nullptr))
+        return fail(POT_ERR_INVALID_ARG, "seg_count and leaf_touched go together");
+    if (o->seg_count && (!is_device_ptr(o->seg_count) || !is_device_ptr(o->leaf_touched)))
+        return fail(POT_ERR_INVALID_ARG, "seg_count / leaf_touched must be device memory");
+    return POT_OK;
+}
+
+void fill_tree_params(RenderParams &p, const pot_tree *t, const pot_render_opts *o)
+{
+    std::memset(&p, 0, sizeof(p));
+    p.child = t->child;
+    p.sigma = t->sigma;
+    p.sh = t->sh;
+    p.depth = t->desc.depth;
+    p.R = 1 << t->desc.depth;
+    for (int a = 0; a < 3; ++a) p.lo[a] = t->desc.bbox_lo[a];
+    p.size = t->desc.bbox_size;
+    p.h = t->h;
+    p.invh = 1.0f / t->h;
+    p.step_cap = 3 * p.R + 16;
+    if (o) {
+        for (int c = 0; c < 3; ++c) p.bg[c] = o->bg[c];
+        p.gamma = o->gamma;
+        p.seg_count = o->seg_count;
+        p.leaf_touched = o->leaf_touched;
+        if (o->max_steps > 0 && o->max_steps < p.step_cap) p.step_cap = o->max_steps;
+    }
+    p.err = device_error_word();
+}
+
+cudaError_t launch_render(const RenderParams &p, const pot_tree *t, bool cams, cudaStream_t s)
+{
+    const bool count = p.seg_count != nullptr;
+    switch (t->desc.leaf_dtype) {
+    case POT_F32: return launch_render_f32(p, t->K, cams, count, s, 0);
+    case POT_F16: return launch_render_f16(p, t->K, cams, count, s, 0);
+    default: return launch_render_bf16(p, t->K, cams, count, s, 0);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pot_version(void) { return 1; }
+
+const char *pot_last_error(void) { return g_msg; }
+
+int64_t pot_launch_count(void) { return g_launches.load(); }
+
+pot_status pot_build_sparse(const pot_build_desc *desc, int64_t n, const uint64_t *morton,
+                            const float *sigma, const float *sh, pot_tree **out, pot_stream stream)
+{
+    pot_status st = check_desc(desc, 12);
+    if (st != POT_OK) return st;
+    if (!out) return fail(POT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > 0x7FFFFFFE) return fail(POT_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+    if (n > 0 && (!morton || !sigma || !sh)) return fail(POT_ERR_INVALID_ARG, "NULL input array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = (desc->sh_degree + 1) * (desc->sh_degree + 1);
+    Tmp tm, ts, th, tf;
+    const void *dm, *ds, *dh;
+    POT_CUDA(stage_in(morton, sizeof(uint64_t) * n, tm, s, &dm), "stage morton");
+    POT_CUDA(stage_in(sigma, sizeof(float) * n, ts, s, &ds), "stage sigma");
+    POT_CUDA(stage_in(sh, sizeof(float) * 3 * K * n, th, s, &dh), "stage sh");
+    POT_CUDA(tf.alloc(sizeof(unsigned), s), "alloc flags");
+    POT_CUDA(cudaMemsetAsync(tf.p, 0, sizeof(unsigned), s), "memset");
+    unsigned *d_flags = static_cast<unsigned *>(tf.p);
+    POT_CUDA(validate_sparse(desc->depth, n, (const uint64_t *)dm, (const float *)ds, d_flags, s),
+             "validate");
+    unsigned flags = 0;
+    POT_CUDA(cudaMemcpyAsync(&flags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "copy flags");
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    if (flags & 1u)
+        return fail(POT_ERR_INVALID_ARG, "morton codes must be strictly increasing and < 8^depth");
+    if (flags & 2u) return fail(POT_ERR_INVALID_ARG, "sigma contains NaN or Inf");
+    return finish_build(desc, n, (const uint64_t *)dm, (const float *)ds, (const float *)dh, d_flags, out, s);
+}
+
+pot_status pot_build(const pot_build_desc *desc, const float *sigma, const float *sh, pot_tree **out,
+                     pot_stream stream)
+{
+    pot_status st = check_desc(desc, 10);
+    if (st != POT_OK) return st;
+    if (!out) return fail(POT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sigma || !sh) return fail(POT_ERR_INVALID_ARG, "NULL input array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = (desc->sh_degree + 1) * (desc->sh_degree + 1);
+    const int64_t vox = 1ll << (3 * desc->depth);
+    Tmp ts, th, tf;
+    const void *ds, *dh;
+    POT_CUDA(stage_in(sigma, sizeof(float) * vox, ts, s, &ds), "stage sigma");
+    POT_CUDA(stage_in(sh, sizeof(float) * 3 * K * vox, th, s, &dh), "stage sh");
+    POT_CUDA(tf.alloc(sizeof(unsigned), s), "alloc flags");
+    POT_CUDA(cudaMemsetAsync(tf.p, 0, sizeof(unsigned), s), "memset");
+    unsigned *d_flags = static_cast<unsigned *>(tf.p);
+    uint64_t *codes = nullptr;
+    float *csig = nullptr, *csh = nullptr;
+    int64_t n = 0;
+    cudaError_t e = compact_dense(desc->depth, desc->sigma_threshold, (const float *)ds, (const float *)dh,
+                                  K, &codes, &csig, &csh, &n, d_flags, s);
+    Tmp fc, fs, fh;  // released after the build
+    fc.p = codes;
+    fc.s = s;
+    fs.p = csig;
+    fs.s = s;
+    fh.p = csh;
+    fh.s = s;
+    if (e != cudaSuccess) return cuda_fail(e, "compact");
+    unsigned flags = 0;
+    POT_CUDA(cudaMemcpyAsync(&flags, d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "copy flags");
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    if (flags & 2u) return fail(POT_ERR_INVALID_ARG, "sigma contains NaN or Inf");
+    return finish_build(desc, n, codes, csig, csh, d_flags, out, s);
+}
+
+pot_status pot_tree_get_info(const pot_tree *t, pot_tree_info *info)
+{
+    if (!t || !info) return fail(POT_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->depth = t->desc.depth;
+    info->sh_degree = t->desc.sh_degree;
+    info->sh_dim = t->K;
+    info->leaf_dtype = t->desc.leaf_dtype;
+    info->n_nodes = t->n_nodes;
+    info->n_leaves = t->n_leaves;
+    info->bytes = t->bytes;
+    info->leaf_bytes = (int64_t)t->elem_bytes * (1 + t->stride);
+    for (int a = 0; a < 3; ++a) info->bbox_lo[a] = t->desc.bbox_lo[a];
+    info->bbox_size = t->desc.bbox_size;
+    info->saturated = t->saturated;
+    info->device = t->device;
+    return POT_OK;
+}
+
+pot_status pot_tree_export(const pot_tree *t, int32_t *child, float *sigma, float *sh, uint64_t *morton,
+                           pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = t->n_leaves;
+    if (child)
+        POT_CUDA(cudaMemcpyAsync(child, t->child, sizeof(int32_t) * 8 * t->n_nodes, cudaMemcpyDefault, s),
+                 "export child");
+    if (morton && n)
+        POT_CUDA(cudaMemcpyAsync(morton, t->morton, sizeof(uint64_t) * n, cudaMemcpyDefault, s),
+                 "export morton");
+    Out os, oh;
+    void *dsig = nullptr, *dsh = nullptr;
+    POT_CUDA(os.bind(sigma, sizeof(float) * n, s, &dsig), "bind sigma");
+    POT_CUDA(oh.bind(sh, sizeof(float) * 3 * t->K * n, s, &dsh), "bind sh");
+    POT_CUDA(export_leaves(t, (float *)dsig, (float *)dsh, s), "export leaves");
+    POT_CUDA(os.finish(s), "copy sigma");
+    POT_CUDA(oh.finish(s), "copy sh");
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_tree_set_values(pot_tree *t, const float *sigma, const float *sh, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (t->n_leaves == 0) return POT_OK;
+    if (!sigma || !sh) return fail(POT_ERR_INVALID_ARG, "NULL input array");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = t->n_leaves;
+    Tmp ts, th, tf;
+    const void *ds, *dh;
+    POT_CUDA(stage_in(sigma, sizeof(float) * n, ts, s, &ds), "stage sigma");
+    POT_CUDA(stage_in(sh, sizeof(float) * 3 * t->K * n, th, s, &dh), "stage sh");
+    POT_CUDA(tf.alloc(sizeof(unsigned), s), "alloc flags");
+    POT_CUDA(cudaMemsetAsync(tf.p, 0, sizeof(unsigned), s), "memset");
+    POT_CUDA(pack_leaves(t, (const float *)ds, (const float *)dh, (unsigned *)tf.p, s), "pack");
+    unsigned flags = 0;
+    POT_CUDA(cudaMemcpyAsync(&flags, tf.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "copy flags");
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    if (flags & 4u) t->saturated = 1;
+    return POT_OK;
+}
+
+pot_status pot_tree_free(pot_tree *t)
+{
+    destroy_tree(t);
+    return POT_OK;
+}
+
+pot_status pot_query(const pot_tree *t, int64_t n, const float *xyz, int32_t *leaf_out, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return POT_OK;
+    if (!xyz || !leaf_out) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp tx;
+    const void *dx;
+    POT_CUDA(stage_in(xyz, sizeof(float) * 3 * n, tx, s, &dx), "stage xyz");
+    Out oo;
+    void *dout;
+    POT_CUDA(oo.bind(leaf_out, sizeof(int32_t) * n, s, &dout), "bind out");
+    POT_CUDA(launch_query(t, n, (const float *)dx, (int32_t *)dout, s), "query");
+    POT_CUDA(oo.finish(s), "copy out");
+    if (oo.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_sh_basis(int32_t K, int64_t n, const float *dirs, float *Y, pot_stream stream)
+{
+    if (K != 1 && K != 4 && K != 9 && K != 16) return fail(POT_ERR_INVALID_ARG, "K must be 1, 4, 9 or 16");
+    if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return POT_OK;
+    if (!dirs || !Y) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp td;
+    const void *dd;
+    POT_CUDA(stage_in(dirs, sizeof(float) * 3 * n, td, s, &dd), "stage dirs");
+    Out oy;
+    void *dy;
+    POT_CUDA(oy.bind(Y, sizeof(float) * K * n, s, &dy), "bind Y");
+    POT_CUDA(launch_sh_basis(K, n, (const float *)dd, (float *)dy, s), "sh_basis");
+    POT_CUDA(oy.finish(s), "copy Y");
+    if (oy.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_render(const pot_tree *t, const pot_camera *cams, int32_t n_cams, const pot_render_opts *opts,
+                      float *rgb, float *t_final, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n_cams < 0) return fail(POT_ERR_INVALID_ARG, "n_cams < 0");
+    if (n_cams == 0) return POT_OK;
+    if (!cams || !rgb) return fail(POT_ERR_INVALID_ARG, "NULL cams or rgb");
+    if (is_device_ptr(cams)) return fail(POT_ERR_INVALID_ARG, "cams must be in host memory");
+    pot_status st = check_opts(opts);
+    if (st != POT_OK) return st;
+    const int W = cams[0].width, H = cams[0].height;
+    if (W <= 0 || H <= 0 || (int64_t)W * H > (1ll << 31))
+        return fail(POT_ERR_INVALID_ARG, "bad image size %dx%d", W, H);
+    for (int c = 0; c < n_cams; ++c) {
+        const pot_camera &k = cams[c];
+        if (k.width != W || k.height != H)
+            return fail(POT_ERR_INVALID_ARG, "all cameras of one call must share width and height");
+        bool ok = std::isfinite(k.fx) && std::isfinite(k.fy) && std::isfinite(k.cx) && std::isfinite(k.cy) &&
+                  k.fx != 0.f && k.fy != 0.f && !std::isnan(k.near) && !std::isnan(k.far) && k.near >= 0.f;
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 4; ++q) ok = ok && std::isfinite(k.c2w[r][q]);
+        if (!ok) return fail(POT_ERR_INVALID_ARG, "camera %d has non-finite or invalid parameters", c);
+    }
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t npix = (int64_t)n_cams * W * H;
+    Tmp scratch;
+    const size_t cam_off = 256;
+    POT_CUDA(scratch.alloc(cam_off + sizeof(pot_camera) * n_cams, s), "alloc scratch");
+    char *sp = static_cast<char *>(scratch.p);
+    POT_CUDA(cudaMemsetAsync(sp, 0, sizeof(unsigned long long), s), "memset");
+    POT_CUDA(cudaMemcpyAsync(sp + cam_off, cams, sizeof(pot_camera) * n_cams, cudaMemcpyHostToDevice, s),
+             "copy cams");
+    Out orgb, otf;
+    void *drgb, *dtf = nullptr;
+    POT_CUDA(orgb.bind(rgb, sizeof(float) * 3 * npix, s, &drgb), "bind rgb");
+    if (t_final) POT_CUDA(otf.bind(t_final, sizeof(float) * npix, s, &dtf), "bind t_final");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
+    p.W = W;
+    p.H = H;
+    p.tiles_x = (W + 7) / 8;
+    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
+    p.n_tiles = p.tiles_per_cam * n_cams;
+    p.rgb = (float *)drgb;
+    p.t_final = (float *)dtf;
+    p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
+    POT_CUDA(launch_render(p, t, true, s), "render");
+    POT_CUDA(orgb.finish(s), "copy rgb");
+    POT_CUDA(otf.finish(s), "copy t_final");
+    if (orgb.host || otf.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_render_rays(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
+                           const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return POT_OK;
+    if (!origins || !dirs || !rgb) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    pot_status st = check_opts(opts);
+    if (st != POT_OK) return st;
+    const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
+    if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp to, td, scratch;
+    const void *dor, *ddr;
+    POT_CUDA(stage_in(origins, sizeof(float) * 3 * n, to, s, &dor), "stage origins");
+    POT_CUDA(stage_in(dirs, sizeof(float) * 3 * n, td, s, &ddr), "stage dirs");
+    POT_CUDA(scratch.alloc(sizeof(unsigned long long), s), "alloc scratch");
+    POT_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), s), "memset");
+    Out orgb, otf;
+    void *drgb, *dtf = nullptr;
+    POT_CUDA(orgb.bind(rgb, sizeof(float) * 3 * n, s, &drgb), "bind rgb");
+    if (t_final) POT_CUDA(otf.bind(t_final, sizeof(float) * n, s, &dtf), "bind t_final");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.ray_o = (const float *)dor;
+    p.ray_d = (const float *)ddr;
+    p.n_rays = n;
+    p.near = near;
+    p.far = far;
+    p.n_tiles = (n + 31) / 32;
+    p.rgb = (float *)drgb;
+    p.t_final = (float *)dtf;
+    p.tile_counter = static_cast<unsigned long long *>(scratch.p);
+    POT_CUDA(launch_render(p, t, false, s), "render_rays");
+    POT_CUDA(orgb.finish(s), "copy rgb");
+    POT_CUDA(otf.finish(s), "copy t_final");
+    if (orgb.host || otf.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_check(pot_stream stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    unsigned int *w = device_error_word();
+    if (!w) return fail(POT_ERR_CUDA, "device error word unavailable");
+    unsigned v = 0;
+    POT_CUDA(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost), "read error word");
+    if (v) {
+        POT_CUDA(cudaMemset(w, 0, sizeof(v)), "clear error word");
+        return fail(POT_ERR_TRAVERSAL, "a ray exceeded its traversal step bound (word 0x%x)", v);
+    }
+    return POT_OK;
+}
+
+}  // extern "C"

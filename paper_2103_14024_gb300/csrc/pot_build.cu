@@ -1,0 +1,443 @@
+// pot_build.cu -- tree construction on the device (Sec. 3.2 "Filtering": the
+// kept voxels become leaves at the deepest level, the tree is empty elsewhere).
+//
+// Input: the kept voxels' Morton codes in ascending order (given, or compacted
+// from a dense grid).  For each level l = D-1 .. 0 the parents' codes are the
+// children's codes >> 3; a scan of "first child of its parent" flags ranks the
+// distinct parents, which are the level's nodes in ascending Morton prefix.
+// Breadth-first offsets of the levels then give every node's index, and one
+// pass per level writes child[node][slot].
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <vector>
+
+#include "pot_device.cuh"
+#include "pot_internal.h"
+
+namespace pot {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Inclusive scan of one value per thread across the block; returns the
+// thread's inclusive prefix and writes the block total to *total.
+__device__ int block_scan_incl(int v, int *total)
+{
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) v += warp_tot[wid - 1];
+    *total = warp_tot[kScanThreads / 32 - 1];
+    __syncthreads();
+    return v;
+}
+
+__global__ void scan_tile_totals(const int *in, int64_t n, int *totals)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    int tot;
+    block_scan_incl(s, &tot);
+    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+// prefix: inclusive scan of the tile totals (NULL for a single tile)
+__global__ void scan_tiles(const int *in, int *out, int64_t n, const int *prefix)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+        v[k] = s;
+    }
+    int tot;
+    int incl = block_scan_incl(s, &tot);
+    int off = incl - s + ((prefix && blockIdx.x > 0) ? prefix[blockIdx.x - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) out[base + k] = v[k] + off;
+}
+
+cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        count_launch();
+        return cudaGetLastError();
+    }
+    int *tot = nullptr;
+    cudaError_t e = cudaMallocAsync(&tot, sizeof(int) * 2 * tiles, s);
+    if (e != cudaSuccess) return e;
+    scan_tile_totals<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, tot);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan_inclusive(tot, tot + tiles, tiles, s);
+    if (e == cudaSuccess) {
+        scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, tot + tiles);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(tot, s);
+    return e;
+}
+
+unsigned grid_for(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b > (1 << 20)) b = 1 << 20;  // grid-stride loops cover the rest
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---- sparse input validation ---------------------------------------------
+__global__ void k_validate(int depth, int64_t n, const uint64_t *codes, const float *sigma,
+                           unsigned *flags)
+{
+    const uint64_t lim = 1ull << (3 * depth);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = codes[i];
+        if (c >= lim || (i > 0 && c <= codes[i - 1])) atomicOr(flags, 1u);
+        if (!isfinite(sigma[i])) atomicOr(flags, 2u);
+    }
+}
+
+// ---- levels ---------------------------------------------------------------
+__global__ void k_heads(int64_t m, const uint64_t *c, int *head)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        head[i] = (i == 0 || (c[i] >> 3) != (c[i - 1] >> 3)) ? 1 : 0;
+}
+
+// rank := inclusive count - 1; the first child of each parent writes the parent's code
+__global__ void k_parents(int64_t m, const uint64_t *c, int *rank, uint64_t *parent_codes)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = rank[i] - 1;
+        rank[i] = r;
+        if (i == 0 || (c[i] >> 3) != (c[i - 1] >> 3)) parent_codes[r] = c[i] >> 3;
+    }
+}
+
+// child[(off_parent + rank[i]) * 8 + (c[i] & 7)] = leaf or node index of entry i
+__global__ void k_children(int64_t m, const uint64_t *c, const int *rank, int32_t *child,
+                           int64_t off_parent, int64_t off_self, int leaves)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = leaves ? (int32_t)(-(i + 1)) : (int32_t)(off_self + i);
+        child[(off_parent + rank[i]) * 8 + (int64_t)(c[i] & 7u)] = v;
+    }
+}
+
+// ---- leaf packing ---------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T to_store(float x, unsigned *flags);
+
+template <>
+__device__ __forceinline__ float to_store<float>(float x, unsigned *)
+{
+    return x;
+}
+
+template <>
+__device__ __forceinline__ __half to_store<__half>(float x, unsigned *flags)
+{
+    __half h = __float2half_rn(x);
+    if (__hisinf(h) && isfinite(x)) {
+        atomicOr(flags, 4u);
+        h = __float2half_rn(x > 0.f ? 65504.f : -65504.f);
+    }
+    return h;
+}
+
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float x, unsigned *flags)
+{
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    if (__hisinf(b) && isfinite(x)) {
+        atomicOr(flags, 4u);
+        b = __ushort_as_bfloat16(x > 0.f ? (unsigned short)0x7F7F : (unsigned short)0xFF7F);
+    }
+    return b;
+}
+
+template <typename T>
+__device__ __forceinline__ float from_store(T x);
+template <>
+__device__ __forceinline__ float from_store<float>(float x)
+{
+    return x;
+}
+template <>
+__device__ __forceinline__ float from_store<__half>(__half x)
+{
+    return __half2float(x);
+}
+template <>
+__device__ __forceinline__ float from_store<__nv_bfloat16>(__nv_bfloat16 x)
+{
+    return __bfloat162float(x);
+}
+
+template <typename T>
+__global__ void k_pack(int64_t n, int K, int stride, const float *sigma, const float *sh, T *sig_out,
+                       T *sh_out, unsigned *flags)
+{
+    const int row = 3 * K;
+    const int64_t total = n * (int64_t)stride;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = j / stride;
+        const int e = (int)(j - i * stride);
+        sh_out[j] = e < row ? to_store<T>(sh[i * row + e], flags) : to_store<T>(0.f, flags);
+        if (e == 0) sig_out[i] = to_store<T>(sigma[i], flags);
+    }
+}
+
+template <typename T>
+__global__ void k_unpack(int64_t n, int K, int stride, const T *sig_in, const T *sh_in, float *sigma,
+                         float *sh)
+{
+    const int row = 3 * K;
+    const int64_t total = n * (int64_t)row;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = j / row;
+        const int e = (int)(j - i * row);
+        if (sh) sh[j] = from_store<T>(sh_in[i * stride + e]);
+        if (sigma && e == 0) sigma[i] = from_store<T>(sig_in[i]);
+    }
+}
+
+// ---- dense compaction -----------------------------------------------------
+__device__ __forceinline__ void morton_decode3(uint64_t m, int depth, int64_t &x, int64_t &y, int64_t &z)
+{
+    x = y = z = 0;
+    for (int b = 0; b < depth; ++b) {
+        x |= (int64_t)((m >> (3 * b + 2)) & 1u) << b;
+        y |= (int64_t)((m >> (3 * b + 1)) & 1u) << b;
+        z |= (int64_t)((m >> (3 * b)) & 1u) << b;
+    }
+}
+
+__global__ void k_dense_flags(int depth, float tau, const float *sigma, int *flag, unsigned *flags)
+{
+    const int64_t R = 1ll << depth;
+    const int64_t total = R * R * R;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < total;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x, y, z;
+        morton_decode3((uint64_t)m, depth, x, y, z);
+        const float s = sigma[(x * R + y) * R + z];
+        if (!isfinite(s)) atomicOr(flags, 2u);
+        flag[m] = s > tau ? 1 : 0;
+    }
+}
+
+__global__ void k_dense_gather(int depth, int K, const float *sigma, const float *sh, const int *incl,
+                               uint64_t *codes, float *sig_out, float *sh_out)
+{
+    const int64_t R = 1ll << depth;
+    const int64_t total = R * R * R;
+    const int row = 3 * K;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < total;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const int prev = m > 0 ? incl[m - 1] : 0;
+        if (incl[m] == prev) continue;
+        int64_t x, y, z;
+        morton_decode3((uint64_t)m, depth, x, y, z);
+        const int64_t v = (x * R + y) * R + z;
+        codes[prev] = (uint64_t)m;
+        sig_out[prev] = sigma[v];
+        for (int e = 0; e < row; ++e) sh_out[(int64_t)prev * row + e] = sh[v * row + e];
+    }
+}
+
+}  // namespace
+
+cudaError_t validate_sparse(int depth, int64_t n, const uint64_t *d_codes, const float *d_sigma,
+                            unsigned int *d_flags, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_validate<<<grid_for(n, 256), 256, 0, s>>>(depth, n, d_codes, d_sigma, d_flags);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t build_levels_and_children(pot_tree *t, int64_t n, const uint64_t *d_codes, cudaStream_t s,
+                                      unsigned int *, int *status)
+{
+    const int D = t->desc.depth;
+    *status = 0;
+    cudaError_t e = cudaSuccess;
+    if (n == 0) {
+        t->n_nodes = 1;
+        e = cudaMalloc(&t->child, sizeof(int32_t) * 8);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->child, 0, sizeof(int32_t) * 8, s);
+        return e;
+    }
+    // per level l (0..D): codes and, for l >= 1, the rank of each entry's parent
+    std::vector<uint64_t *> codes(D + 1, nullptr);
+    std::vector<int *> rank(D + 1, nullptr);
+    std::vector<int64_t> cnt(D + 1, 0);
+    codes[D] = const_cast<uint64_t *>(d_codes);
+    cnt[D] = n;
+    for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int64_t m = cnt[l + 1];
+        e = cudaMallocAsync(&rank[l + 1], sizeof(int) * m, s);
+        if (e != cudaSuccess) break;
+        k_heads<<<grid_for(m, 256), 256, 0, s>>>(m, codes[l + 1], rank[l + 1]);
+        count_launch();
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = scan_inclusive(rank[l + 1], rank[l + 1], m, s);
+        int np = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&np, rank[l + 1] + (m - 1), sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        cnt[l] = np;
+        e = cudaMallocAsync(&codes[l], sizeof(uint64_t) * (np > 0 ? np : 1), s);
+        if (e != cudaSuccess) break;
+        k_parents<<<grid_for(m, 256), 256, 0, s>>>(m, codes[l + 1], rank[l + 1], codes[l]);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && cnt[0] != 1) *status = 1;  // cannot happen for valid codes
+    std::vector<int64_t> off(D + 1, 0);
+    for (int l = 1; l <= D; ++l) off[l] = off[l - 1] + cnt[l - 1];
+    const int64_t N = off[D];
+    if (e == cudaSuccess && N >= (int64_t)0x7FFFFFFF) *status = 2;
+    if (e == cudaSuccess && *status == 0) {
+        t->n_nodes = N;
+        e = cudaMalloc(&t->child, sizeof(int32_t) * 8 * N);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t->child, 0, sizeof(int32_t) * 8 * N, s);
+        for (int l = 0; l < D && e == cudaSuccess; ++l) {
+            const int64_t m = cnt[l + 1];
+            k_children<<<grid_for(m, 256), 256, 0, s>>>(m, codes[l + 1], rank[l + 1], t->child, off[l],
+                                                        off[l + 1], l + 1 == D);
+            count_launch();
+            e = cudaGetLastError();
+        }
+    }
+    for (int l = 0; l <= D; ++l) {
+        if (l < D && codes[l]) cudaFreeAsync(codes[l], s);
+        if (rank[l]) cudaFreeAsync(rank[l], s);
+    }
+    return e;
+}
+
+cudaError_t pack_leaves(pot_tree *t, const float *d_sigma, const float *d_sh, unsigned int *d_flags,
+                        cudaStream_t s)
+{
+    const int64_t n = t->n_leaves;
+    const int64_t sig_bytes = ((n * t->elem_bytes + 255) / 256) * 256;
+    const int64_t sh_bytes = n * t->stride * t->elem_bytes;
+    cudaError_t e = cudaSuccess;
+    if (!t->sigma) e = cudaMalloc(&t->sigma, sig_bytes > 0 ? sig_bytes : 256);
+    if (e == cudaSuccess && !t->sh) e = cudaMalloc(&t->sh, sh_bytes > 0 ? sh_bytes : 256);
+    if (e != cudaSuccess || n == 0) return e;
+    const unsigned g = grid_for(n * t->stride, 256);
+    switch (t->desc.leaf_dtype) {
+    case POT_F32:
+        k_pack<float><<<g, 256, 0, s>>>(n, t->K, t->stride, d_sigma, d_sh, (float *)t->sigma,
+                                         (float *)t->sh, d_flags);
+        break;
+    case POT_F16:
+        k_pack<__half><<<g, 256, 0, s>>>(n, t->K, t->stride, d_sigma, d_sh, (__half *)t->sigma,
+                                          (__half *)t->sh, d_flags);
+        break;
+    default:
+        k_pack<__nv_bfloat16><<<g, 256, 0, s>>>(n, t->K, t->stride, d_sigma, d_sh,
+                                                 (__nv_bfloat16 *)t->sigma, (__nv_bfloat16 *)t->sh,
+                                                 d_flags);
+        break;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t export_leaves(const pot_tree *t, float *d_sigma, float *d_sh, cudaStream_t s)
+{
+    const int64_t n = t->n_leaves;
+    if (n == 0 || (!d_sigma && !d_sh)) return cudaSuccess;
+    const unsigned g = grid_for(n * 3 * t->K, 256);
+    switch (t->desc.leaf_dtype) {
+    case POT_F32:
+        k_unpack<float><<<g, 256, 0, s>>>(n, t->K, t->stride, (const float *)t->sigma,
+                                           (const float *)t->sh, d_sigma, d_sh);
+        break;
+    case POT_F16:
+        k_unpack<__half><<<g, 256, 0, s>>>(n, t->K, t->stride, (const __half *)t->sigma,
+                                            (const __half *)t->sh, d_sigma, d_sh);
+        break;
+    default:
+        k_unpack<__nv_bfloat16><<<g, 256, 0, s>>>(n, t->K, t->stride, (const __nv_bfloat16 *)t->sigma,
+                                                   (const __nv_bfloat16 *)t->sh, d_sigma, d_sh);
+        break;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t compact_dense(int depth, float tau, const float *d_sigma, const float *d_sh, int K,
+                          uint64_t **d_codes, float **d_sig_out, float **d_sh_out, int64_t *n_out,
+                          unsigned int *d_flags, cudaStream_t s)
+{
+    const int64_t total = 1ll << (3 * depth);
+    int *incl = nullptr;
+    cudaError_t e = cudaMallocAsync(&incl, sizeof(int) * total, s);
+    if (e != cudaSuccess) return e;
+    k_dense_flags<<<grid_for(total, 256), 256, 0, s>>>(depth, tau, d_sigma, incl, d_flags);
+    count_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan_inclusive(incl, incl, total, s);
+    int n = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, incl + (total - 1), sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        *n_out = n;
+        e = cudaMallocAsync(d_codes, sizeof(uint64_t) * (n > 0 ? n : 1), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(d_sig_out, sizeof(float) * (n > 0 ? n : 1), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(d_sh_out, sizeof(float) * 3 * K * (int64_t)(n > 0 ? n : 1), s);
+    }
+    if (e == cudaSuccess && n > 0) {
+        k_dense_gather<<<grid_for(total, 256), 256, 0, s>>>(depth, K, d_sigma, d_sh, incl, *d_codes,
+                                                            *d_sig_out, *d_sh_out);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(incl, s);
+    return e;
+}
+
+}  // namespace pot

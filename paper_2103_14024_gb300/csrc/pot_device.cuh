@@ -1,0 +1,276 @@
+// pot_device.cuh -- device helpers of the PlenOctree render path (sm_103a).
+//
+// Geometry is fp32 throughout.  Plane-crossing times and plane-side tests use
+// error-free transformations (TwoSum, TwoProd via fma) so that a crossing time
+// is known to about 2^-46 relative and a segment length delta = t_exit - t to
+// about 2^-24 of delta itself.  Plain fp32 times would carry an absolute error
+// of about one ulp of t (~5e-7 at t ~ 4), which, multiplied by densities in the
+// thousands, would move a pixel by more than 1e-4.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pot {
+
+constexpr int kMaxDepth = 12;
+
+// ------------------------------------------------------------------------
+// error-free transformations
+// ------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (a - b) rounded once: hi parts cancel exactly when close.
+__device__ __forceinline__ float df_sub(df a, df b)
+{
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+
+__device__ __forceinline__ bool df_lt(df a, df b) { return df_sub(a, b) < 0.f; }
+
+// Time t at which o + t d crosses plane k of one axis, i.e.
+// (lo + k h - o) / d, with A = lo - o given exactly as Ahi + Alo and rd = 1/d.
+__device__ __forceinline__ df cross_time(int k, float h, float Ahi, float Alo, float d, float rd)
+{
+    float p, pe;
+    two_prod((float)k, h, p, pe);
+    float s, e;
+    two_sum(Ahi, p, s, e);
+    float rest = __fadd_rn(__fadd_rn(Alo, pe), e);
+    float t = __fmul_rn(s, rd);
+    float r = __fadd_rn(__fmaf_rn(-t, d, s), rest);
+    return {t, __fmul_rn(r, rd)};
+}
+
+// (o + t d) - (lo + k h) on one axis, to ~2^-46 relative: only its sign is used.
+__device__ __forceinline__ float pos_minus_plane(df t, float d, float Ahi, float Alo, int k, float h)
+{
+    float p1, e1;
+    two_prod(t.hi, d, p1, e1);
+    float p2, e2;
+    two_prod((float)k, h, p2, e2);
+    float s, es;
+    two_sum(p1, -Ahi, s, es);
+    float s2, es2;
+    two_sum(s, -p2, s2, es2);
+    float rest = __fsub_rn(__fadd_rn(__fadd_rn(es, es2), __fadd_rn(e1, __fmul_rn(t.lo, d))),
+                           __fadd_rn(Alo, e2));
+    return __fadd_rn(s2, rest);
+}
+
+// Voxel index on one axis of the point o + t d; a point on a face goes to the
+// side the ray is heading (d < 0: lower voxel).  ``margin`` bounds the error of
+// the fp32 estimate in voxel units; only near a face is the exact test run.
+__device__ __forceinline__ int locate_axis(df t, float d, float Ahi, float Alo, float h, float invh,
+                                           float margin)
+{
+    float ug = __fmul_rn(__fmaf_rn(t.hi, d, -Ahi), invh);
+    float kn = rintf(ug);
+    float fr = __fsub_rn(ug, kn);
+    int k = (int)kn;
+    if (fabsf(fr) > margin) return fr > 0.f ? k : k - 1;
+    float v = pos_minus_plane(t, d, Ahi, Alo, k, h);
+    if (v > 0.f) return k;
+    if (v < 0.f) return k - 1;
+    return d < 0.f ? k - 1 : k;
+}
+
+// Exact sign of (p - lo) - k h for fp32 p, lo, h and an integer k (|k| < 2^24):
+// the four exact terms are summed into a non-overlapping expansion whose most
+// significant non-zero component carries the sign.
+__device__ __forceinline__ int sign_point_minus_plane(float p, float lo, int k, float h)
+{
+    float s1, e1;
+    two_sum(p, -lo, s1, e1);
+    float q1, q0;
+    two_prod((float)k, h, q1, q0);
+    float Q, a0, a1, a2, b0, b1, b2, b3;
+    two_sum(-q0, e1, Q, a0);
+    two_sum(Q, s1, a2, a1);
+    two_sum(-q1, a0, Q, b0);
+    two_sum(Q, a1, Q, b1);
+    two_sum(Q, a2, b3, b2);
+    if (b3 != 0.f) return b3 > 0.f ? 1 : -1;
+    if (b2 != 0.f) return b2 > 0.f ? 1 : -1;
+    if (b1 != 0.f) return b1 > 0.f ? 1 : -1;
+    if (b0 != 0.f) return b0 > 0.f ? 1 : -1;
+    return 0;
+}
+
+// Exact voxel coordinate of p on one axis, or -1 / R when outside [lo, lo + R h).
+__device__ __forceinline__ int voxel_exact(float p, float lo, float h, float invh, int R)
+{
+    if (!(p == p)) return -1;
+    float g = floorf(__fmul_rn(__fsub_rn(p, lo), invh));
+    int k = (int)fminf(fmaxf(g, -1.f), (float)R);
+    for (int it = 0; it < 4 && k >= 0 && sign_point_minus_plane(p, lo, k, h) < 0; ++it) --k;
+    for (int it = 0; it < 4 && k < R && sign_point_minus_plane(p, lo, k + 1, h) >= 0; ++it) ++k;
+    if (k < 0) return -1;
+    if (k >= R) return R;
+    return k;
+}
+
+// ------------------------------------------------------------------------
+// real spherical harmonics, degree <= 3 (App. B.1), polynomial form
+// ------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr double csqrt_iter(double x, double g, int n)
+{
+    return n == 0 ? g : csqrt_iter(x, 0.5 * (g + x / g), n - 1);
+}
+constexpr double csqrt(double x) { return csqrt_iter(x, x > 1.0 ? x : 1.0, 64); }
+
+// Constants of the real basis: sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the
+// Legendre polynomial's leading factor, reduced to Cartesian monomials of the
+// unit direction (x, y, z); every sign is + (Condon-Shortley phase cancelled by
+// the (-1)^m of the real basis).
+struct ShC {
+    static constexpr float c0 = (float)(0.5 * csqrt(1.0 / kPi));
+    static constexpr float c1 = (float)csqrt(3.0 / (4.0 * kPi));
+    static constexpr float c2a = (float)(0.5 * csqrt(15.0 / kPi));
+    static constexpr float c2b = (float)(0.25 * csqrt(5.0 / kPi));
+    static constexpr float c2c = (float)(0.25 * csqrt(15.0 / kPi));
+    static constexpr float c3a = (float)(0.25 * csqrt(35.0 / (2.0 * kPi)));
+    static constexpr float c3b = (float)(0.5 * csqrt(105.0 / kPi));
+    static constexpr float c3c = (float)(0.25 * csqrt(21.0 / (2.0 * kPi)));
+    static constexpr float c3d = (float)(0.25 * csqrt(7.0 / kPi));
+    static constexpr float c3e = (float)(0.25 * csqrt(105.0 / kPi));
+};
+
+template <int K>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
+{
+    Y[0] = ShC::c0;
+    if (K > 1) {
+        Y[1] = ShC::c1 * y;
+        Y[2] = ShC::c1 * z;
+        Y[3] = ShC::c1 * x;
+    }
+    if (K > 4) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = ShC::c2a * x * y;
+        Y[5] = ShC::c2a * y * z;
+        Y[6] = ShC::c2b * (3.f * zz - 1.f);
+        Y[7] = ShC::c2a * x * z;
+        Y[8] = ShC::c2c * (xx - yy);
+        if (K > 9) {
+            Y[9] = ShC::c3a * y * (3.f * xx - yy);
+            Y[10] = ShC::c3b * x * y * z;
+            Y[11] = ShC::c3c * y * (5.f * zz - 1.f);
+            Y[12] = ShC::c3d * z * (5.f * zz - 3.f);
+            Y[13] = ShC::c3c * x * (5.f * zz - 1.f);
+            Y[14] = ShC::c3e * z * (xx - yy);
+            Y[15] = ShC::c3a * x * (xx - 3.f * yy);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// leaf storage: sigma [L] and SH records [L][stride] (16-byte aligned rows)
+// ------------------------------------------------------------------------
+template <typename T>
+struct Store;
+
+template <>
+struct Store<float> {
+    static constexpr int kVec = 4;  // elements per 16-byte load
+    __device__ static __forceinline__ float load_sigma(const float *s, int64_t i) { return __ldg(s + i); }
+    __device__ static __forceinline__ void unpack(uint4 r, float *f)
+    {
+        f[0] = __uint_as_float(r.x);
+        f[1] = __uint_as_float(r.y);
+        f[2] = __uint_as_float(r.z);
+        f[3] = __uint_as_float(r.w);
+    }
+};
+
+template <>
+struct Store<__half> {
+    static constexpr int kVec = 8;
+    __device__ static __forceinline__ float load_sigma(const __half *s, int64_t i)
+    {
+        return __half2float(__ldg(s + i));
+    }
+    __device__ static __forceinline__ void unpack(uint4 r, float *f)
+    {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            __half2 h2 = *reinterpret_cast<const __half2 *>(&w[j]);
+            float2 v = __half22float2(h2);
+            f[2 * j] = v.x;
+            f[2 * j + 1] = v.y;
+        }
+    }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+    static constexpr int kVec = 8;
+    __device__ static __forceinline__ float load_sigma(const __nv_bfloat16 *s, int64_t i)
+    {
+        return __bfloat162float(__ldg(s + i));
+    }
+    __device__ static __forceinline__ void unpack(uint4 r, float *f)
+    {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            f[2 * j] = __uint_as_float(w[j] << 16);
+            f[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+        }
+    }
+};
+
+// Elements per padded SH record for K coefficients per channel.
+template <typename T>
+__host__ __device__ constexpr int sh_stride(int K)
+{
+    return (3 * K + Store<T>::kVec - 1) / Store<T>::kVec * Store<T>::kVec;
+}
+
+// x_c = sum_k sh[k][c] Y_k for the three channels of one leaf.
+template <int K, typename T>
+__device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const float *Y, float *x)
+{
+    constexpr int V = Store<T>::kVec;
+    constexpr int N = 3 * K;
+    constexpr int NV = (N + V - 1) / V;
+    const uint4 *p = reinterpret_cast<const uint4 *>(sh + leaf * (int64_t)(NV * V));
+    uint4 raw[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) raw[v] = __ldg(p + v);
+    x[0] = x[1] = x[2] = 0.f;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        float f[V];
+        Store<T>::unpack(raw[v], f);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int idx = v * V + e;
+            if (idx < N) x[idx % 3] = fmaf(f[e], Y[idx / 3], x[idx % 3]);
+        }
+    }
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return __frcp_rn(1.f + __expf(-x)); }
+
+}  // namespace pot

@@ -1,0 +1,87 @@
+// pot_internal.h -- types shared by the library's host code and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pot.h"
+
+struct pot_tree {
+    int device;
+    pot_build_desc desc;
+    int K;              // SH coefficients per channel
+    int stride;         // elements per padded SH record
+    int elem_bytes;     // 4 (f32) or 2 (f16 / bf16)
+    int64_t n_nodes;
+    int64_t n_leaves;
+    float h;            // voxel edge, bbox_size / 2^D (exact)
+    int32_t *child;     // [n_nodes][8]
+    void *sigma;        // [n_leaves]          leaf dtype
+    void *sh;           // [n_leaves][stride]  leaf dtype
+    uint64_t *morton;   // [n_leaves]
+    int64_t bytes;
+    int saturated;
+};
+
+namespace pot {
+
+// Everything a render launch needs; passed by value.
+struct RenderParams {
+    const int32_t *child;
+    const void *sigma;
+    const void *sh;
+    int depth;
+    int R;
+    float lo[3];
+    float size;
+    float h;
+    float invh;
+    float bg[3];
+    float gamma;
+    int step_cap;
+    // ray source: cameras (tiles of 8 x 4 pixels) or explicit rays (32 per tile)
+    const pot_camera *cams;
+    int W, H;
+    int tiles_x;
+    int64_t tiles_per_cam;
+    const float *ray_o;
+    const float *ray_d;
+    int64_t n_rays;
+    float near, far;
+    int64_t n_tiles;
+    // outputs
+    float *rgb;
+    float *t_final;
+    int32_t *seg_count;
+    uint8_t *leaf_touched;
+    // scratch
+    unsigned long long *tile_counter;
+    unsigned int *err;
+};
+
+// Launches (defined in pot_render_*.cu); return the CUDA error of the launch.
+cudaError_t launch_render_f32(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
+                              int max_blocks);
+cudaError_t launch_render_f16(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
+                              int max_blocks);
+cudaError_t launch_render_bf16(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
+                               int max_blocks);
+
+// Build / query / export helpers (pot_build.cu, pot_query.cu).
+cudaError_t build_levels_and_children(pot_tree *t, int64_t n, const uint64_t *d_codes, cudaStream_t s,
+                                      unsigned int *d_flags, int *status);
+cudaError_t validate_sparse(int depth, int64_t n, const uint64_t *d_codes, const float *d_sigma,
+                            unsigned int *d_flags, cudaStream_t s);
+cudaError_t compact_dense(int depth, float tau, const float *d_sigma, const float *d_sh, int K,
+                          uint64_t **d_codes, float **d_sig_out, float **d_sh_out, int64_t *n_out,
+                          unsigned int *d_flags, cudaStream_t s);
+cudaError_t pack_leaves(pot_tree *t, const float *d_sigma, const float *d_sh, unsigned int *d_flags,
+                        cudaStream_t s);
+cudaError_t export_leaves(const pot_tree *t, float *d_sigma, float *d_sh, cudaStream_t s);
+cudaError_t launch_query(const pot_tree *t, int64_t n, const float *xyz, int32_t *out, cudaStream_t s);
+cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaStream_t s);
+
+unsigned int *device_error_word();   // per-device word raised by kernels
+void count_launch(int n = 1);
+
+}  // namespace pot

@@ -1,0 +1,275 @@
+// pot_render.cuh -- forward render kernel of the PlenOctree path (sm_103a).
+//
+// One warp renders one tile of 32 rays at a time (8 x 4 pixels of a camera,
+// or 32 consecutive explicit rays); warps take tiles from a global counter
+// until none is left (persistent grid, one wave of resident blocks).  Per ray:
+//   a1 pinhole ray (fp32 expression of the public header)
+//   a2 clip to the tree box and to [near, far]
+//   a3 locate the cell: descend the child array from the deepest ancestor the
+//      new voxel shares with the previous one (ancestor stack in shared memory)
+//   a4 exit time of the cell (double-float plane crossings); an empty node of
+//      any size is crossed in one step (Sec. 3.2 "Rendering")
+//   a5 leaf fetch: sigma and the SH record in 16-byte vector loads
+//   a6 colour: sigmoid of the SH dot product, basis evaluated once per ray
+//      because it is constant along the ray (App. B.3.2)
+//   a7 composite: w = T (1 - exp(-max(sigma,0) delta)), C += w c (Eq. 1)
+//   a8 stop once T < gamma (Sec. 3.2), add T * bg (App. B.3.2), store.
+#pragma once
+
+#include "pot_device.cuh"
+#include "pot_internal.h"
+
+namespace pot {
+
+constexpr int kBlock = 256;
+
+template <int K, typename T, bool COUNT>
+__device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
+                                          int32_t *stk, const float o[3], const float d[3], float near,
+                                          float far, float col[3], float &Tr, int &nseg)
+{
+    const int D = p.depth;
+    const int R = p.R;
+    const float h = p.h, invh = p.invh;
+    const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+    if (!(len > 0.f) || !(len < 3.0e38f)) return;
+    const float invlen = __frcp_rn(len);
+
+    float Y[K];
+    sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y);
+
+    float Ahi[3], Alo[3], rd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
+        rd[a] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
+    }
+
+    // a2: clip range in units of the ray parameter t (position o + t d)
+    df tin = {near * invlen, 0.f};
+    df tout = {far * invlen, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.f) {
+            float s, e;
+            two_sum(o[a], -p.lo[a], s, e);
+            const bool inside = (s > 0.f || (s == 0.f && e >= 0.f)) && (s < p.size || (s == p.size && e < 0.f));
+            if (!inside) return;
+        } else {
+            df t0 = cross_time(0, h, Ahi[a], Alo[a], d[a], rd[a]);
+            df t1 = cross_time(R, h, Ahi[a], Alo[a], d[a], rd[a]);
+            if (d[a] < 0.f) {
+                df tmp = t0;
+                t0 = t1;
+                t1 = tmp;
+            }
+            if (df_lt(tin, t0)) tin = t0;
+            if (df_lt(t1, tout)) tout = t1;
+        }
+    }
+    if (!df_lt(tin, tout)) return;
+
+    // error bound of the fp32 voxel-coordinate estimate, in voxels
+    float margin[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        margin[a] = (fabsf(tout.hi * d[a]) + fabsf(Ahi[a])) * invh * 3.8146973e-6f + 1e-6f;
+
+    int q[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = locate_axis(tin, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+        q[a] = min(max(v, 0), R - 1);
+    }
+
+    df t = tin;
+    int lvl_valid = 0;  // stack entries 0..lvl_valid hold the path of the current voxel
+    stk[0] = 0;
+    int qp[3] = {q[0], q[1], q[2]};
+    for (int step = 0;; ++step) {
+        // a3: descend from the deepest shared ancestor
+        const unsigned diff = (unsigned)((q[0] ^ qp[0]) | (q[1] ^ qp[1]) | (q[2] ^ qp[2]));
+        const int lc = diff ? D - 32 + __clz(diff) : D - 1;  // level of the common ancestor
+        int l = min(lc, lvl_valid);
+        int node = stk[l * kBlock];
+        int leaf = -1, cell_lvl = D;
+        for (; l < D; ++l) {
+            const int b = D - 1 - l;
+            const int s = (((q[0] >> b) & 1) << 2) | (((q[1] >> b) & 1) << 1) | ((q[2] >> b) & 1);
+            const int c = __ldg(p.child + (int64_t)node * 8 + s);
+            if (c > 0 && l < D - 1) {
+                node = c;
+                stk[(l + 1) * kBlock] = c;
+                continue;
+            }
+            if (c < 0) leaf = -c - 1;
+            else cell_lvl = l + 1;
+            break;
+        }
+        lvl_valid = min(l, D - 1);
+
+        // a4: exit of the cell
+        const int sz = 1 << (D - cell_lvl);
+        int qb[3];
+        df texit = {__int_as_float(0x7f800000), 0.f};
+        int ax = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            qb[a] = q[a] & ~(sz - 1);
+            if (d[a] != 0.f) {
+                const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
+                const df tb = cross_time(k, h, Ahi[a], Alo[a], d[a], rd[a]);
+                if (df_lt(tb, texit)) {
+                    texit = tb;
+                    ax = a;
+                }
+            }
+        }
+        const bool last = !df_lt(texit, tout);
+        const df tend = last ? tout : texit;
+        const float dt = df_sub(tend, t);
+
+        if (leaf >= 0 && dt > 0.f) {
+            // a5..a7
+            const float delta = dt * len;
+            const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
+            float x[3];
+            leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
+            const float e = expf(-sig * delta);
+            const float w = Tr * (1.f - e);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) col[c] = fmaf(w, sigmoidf_(x[c]), col[c]);
+            Tr *= e;
+            if (COUNT) {
+                ++nseg;
+                p.leaf_touched[leaf] = 1;
+            }
+            if (Tr < p.gamma) break;  // a8 early stop (gamma = 0 never stops)
+        }
+        if (last) break;
+        if (step >= p.step_cap) {
+            atomicOr(p.err, 1u);
+            break;
+        }
+        // next voxel: the exit axis steps by one cell; the other axes are
+        // located at t_exit within the current cell's face, never backwards
+        int nq[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == ax) {
+                nq[a] = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
+            } else if (d[a] == 0.f) {
+                nq[a] = q[a];
+            } else {
+                int v = locate_axis(texit, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+                v = min(max(v, qb[a]), qb[a] + sz - 1);
+                nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
+            }
+        }
+        if (nq[ax] < 0 || nq[ax] >= R) break;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            qp[a] = q[a];
+            q[a] = nq[a];
+        }
+        if (df_lt(t, texit)) t = texit;
+    }
+}
+
+template <int K, typename T, bool CAMS, bool COUNT>
+__global__ void __launch_bounds__(kBlock) render_kernel(const RenderParams p)
+{
+    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
+    int32_t *stk = &stk_sh[0][threadIdx.x];
+    const int lane = threadIdx.x & 31;
+    const T *sig_arr = static_cast<const T *>(p.sigma);
+    const T *sh_arr = static_cast<const T *>(p.sh);
+
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1ull);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= (unsigned long long)p.n_tiles) break;
+
+        float o[3], d[3], near, far;
+        int64_t ray;
+        bool valid;
+        if (CAMS) {
+            const int64_t cam = (int64_t)tile / p.tiles_per_cam;
+            const int64_t rem = (int64_t)tile - cam * p.tiles_per_cam;
+            const int ty = (int)(rem / p.tiles_x);
+            const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
+            const int i = tx * 8 + (lane & 7);
+            const int j = ty * 4 + (lane >> 3);
+            valid = i < p.W && j < p.H;
+            ray = (cam * p.H + j) * p.W + i;
+            const pot_camera *c = p.cams + cam;
+            // a1: pixel ray, each operation rounded once in the stated order
+            const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), c->cx), c->fx);
+            const float yc = -__fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), c->cy), c->fy);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                d[r] = __fsub_rn(__fadd_rn(__fmul_rn(c->c2w[r][0], xc), __fmul_rn(c->c2w[r][1], yc)),
+                                 c->c2w[r][2]);
+                o[r] = c->c2w[r][3];
+            }
+            near = c->near;
+            far = c->far;
+        } else {
+            ray = (int64_t)tile * 32 + lane;
+            valid = ray < p.n_rays;
+            if (valid) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    o[r] = __ldg(p.ray_o + 3 * ray + r);
+                    d[r] = __ldg(p.ray_d + 3 * ray + r);
+                }
+            }
+            near = p.near;
+            far = p.far;
+        }
+        if (valid) {
+            float col[3] = {0.f, 0.f, 0.f};
+            float Tr = 1.f;
+            int nseg = 0;
+            trace_ray<K, T, COUNT>(p, sig_arr, sh_arr, stk, o, d, near, far, col, Tr, nseg);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p.rgb[3 * ray + c] = fmaf(Tr, p.bg[c], col[c]);
+            if (p.t_final) p.t_final[ray] = Tr;
+            if (COUNT) p.seg_count[ray] = nseg;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_render_t(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
+                            int max_blocks)
+{
+    using Fn = void (*)(const RenderParams);
+    Fn fn = nullptr;
+#define POT_PICK(KK)                                                                            \
+    if (K == KK)                                                                                \
+        fn = cams ? (count ? render_kernel<KK, T, true, true> : render_kernel<KK, T, true, false>) \
+                  : (count ? render_kernel<KK, T, false, true> : render_kernel<KK, T, false, false>);
+    POT_PICK(1)
+    POT_PICK(4)
+    POT_PICK(9)
+    POT_PICK(16)
+#undef POT_PICK
+    if (!fn) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (p.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
+    if (blocks > need) blocks = need;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    fn<<<(unsigned)blocks, kBlock, 0, s>>>(p);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pot
