@@ -182,6 +182,27 @@ pot_status pot_render(const pot_tree *tree, const pot_camera *cams, int32_t n_ca
 pot_status pot_render_rays(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
                            const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
 
+/* pot_render for callers that may not allocate GPU memory (the paper has no
+ * counterpart; this is a deployment variant).  Applications that embed the
+ * renderer and own all GPU memory -- a viewer on a fixed memory budget, a host
+ * whose allocator hooks refuse allocations by libraries, a frame loop that
+ * cannot pay for an allocator call -- cannot use pot_render, which allocates a
+ * small scratch buffer (tile counter + device copy of the cameras) per call.
+ * This call takes that scratch from one fixed array inside the library
+ * (256 B + 1024 camera records = 82,176 B per GPU, held until the process
+ * exits) and makes no allocation at all.
+ *   - Same arguments and results as pot_render, except: at most 1024 cameras
+ *     per call (more gives POT_ERR_INVALID_ARG), and rgb / t_final must be
+ *     device memory (nothing is staged); cams are in host memory.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture on the device.
+ *   - All calls share the array and it keeps the last call's contents (the
+ *     tile counter is cleared by every call).  Calls whose GPU work overlaps
+ *     (other streams, other host threads) race on it: serialise them.       */
+pot_status pot_render_noalloc(const pot_tree *tree, const pot_camera *cams, int32_t n_cams,
+                              const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
+
 /* Number of CUDA kernels launched by this library in this process since it
  * was loaded (a counter for benchmarks). */
 int64_t pot_launch_count(void);

@@ -278,6 +278,8 @@ cudaError_t launch_render(const RenderParams &p, const pot_tree *t, bool cams, c
 
 }  // namespace
 
+void pot::set_last_error(const char *msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+
 extern "C" {
 
 int32_t pot_version(void) { return 1; }

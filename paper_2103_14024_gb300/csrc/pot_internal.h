@@ -82,6 +82,7 @@ cudaError_t launch_query(const pot_tree *t, int64_t n, const float *xyz, int32_t
 cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaStream_t s);
 
 unsigned int *device_error_word();   // per-device word raised by kernels
+void set_last_error(const char *msg); // message returned by pot_last_error on this thread
 void count_launch(int n = 1);
 
 }  // namespace pot
