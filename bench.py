@@ -35,8 +35,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 8-view capture (3.940 GB dram read+write) x 25 = 200-view launch
-    "f32": {"sha": "c884ff04d87f9b0e", "bytes_per_launch": 98.50e9},
+    # 8-view capture (4.310 GB read + 0.071 GB written) x 25 = 200-view launch
+    "f32": {"sha": "142654ef392409bb", "bytes_per_launch": 109.53e9},
 }
 
 

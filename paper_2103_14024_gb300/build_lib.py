@@ -50,6 +50,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     deps = _deps()
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    # tuning knobs, e.g. POT_NVCC_EXTRA="-DPOT_RENDER_MIN_BLOCKS=4" (forces a rebuild when set)
+    knobs = os.environ.get("POT_NVCC_EXTRA", "").split()
+    extra += knobs
+    force = force or bool(knobs)
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")

@@ -247,30 +247,52 @@ __host__ __device__ constexpr int sh_stride(int K)
     return (3 * K + Store<T>::kVec - 1) / Store<T>::kVec * Store<T>::kVec;
 }
 
-// x_c = sum_k sh[k][c] Y_k for the three channels of one leaf.
+// x_c = sum_k sh[k][c] Y_k for the three channels of one leaf; the record is
+// read in chunks of up to four 16-byte loads to bound live registers (the
+// lines were prefetched into L1 a step earlier).
 template <int K, typename T>
 __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const float *Y, float *x)
 {
     constexpr int V = Store<T>::kVec;
     constexpr int N = 3 * K;
     constexpr int NV = (N + V - 1) / V;
+    constexpr int CH = 4;
     const uint4 *p = reinterpret_cast<const uint4 *>(sh + leaf * (int64_t)(NV * V));
-    uint4 raw[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) raw[v] = __ldg(p + v);
     x[0] = x[1] = x[2] = 0.f;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        float f[V];
-        Store<T>::unpack(raw[v], f);
+    for (int v0 = 0; v0 < NV; v0 += CH) {
+        uint4 raw[CH];
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int idx = v * V + e;
-            if (idx < N) x[idx % 3] = fmaf(f[e], Y[idx / 3], x[idx % 3]);
+        for (int j = 0; j < CH; ++j)
+            if (v0 + j < NV) raw[j] = __ldg(p + v0 + j);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            if (v0 + j < NV) {
+                float f[V];
+                Store<T>::unpack(raw[j], f);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    const int idx = (v0 + j) * V + e;
+                    if (idx < N) x[idx % 3] = fmaf(f[e], Y[idx / 3], x[idx % 3]);
+                }
+            }
         }
     }
 }
 
-__device__ __forceinline__ float sigmoidf_(float x) { return __frcp_rn(1.f + __expf(-x)); }
+// Ask L1 for the lines of one leaf (SH record and sigma) ahead of its use.
+template <int K, typename T>
+__device__ __forceinline__ void prefetch_leaf(const T *sig, const T *sh, int64_t leaf)
+{
+    constexpr int bytes = sh_stride<T>(K) * (int)sizeof(T);
+    const char *r = reinterpret_cast<const char *>(sh + leaf * (int64_t)sh_stride<T>(K));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
+    if (bytes > 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(r + bytes - 1));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(sig + leaf));
+}
+
+// 1 / (1 + e^-x); x is clamped at -80 (sigmoid < 2e-35) so the divisor stays
+// below 2^126, where the fast division is accurate to 2 ulp.
+__device__ __forceinline__ float sigmoidf_(float x) { return __fdividef(1.f, 1.f + __expf(-fmaxf(x, -80.f))); }
 
 }  // namespace pot

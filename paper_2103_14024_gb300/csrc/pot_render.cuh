@@ -22,6 +22,9 @@
 namespace pot {
 
 constexpr int kBlock = 256;
+#ifndef POT_RENDER_MIN_BLOCKS
+#define POT_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
+#endif
 
 template <int K, typename T, bool COUNT>
 __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
@@ -82,20 +85,20 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
         q[a] = min(max(v, 0), R - 1);
     }
 
-    df t = tin;
-    int lvl_valid = 0;  // stack entries 0..lvl_valid hold the path of the current voxel
+    // a3: descend to the cell of voxel nq from the deepest ancestor it shares
+    // with voxel pq (whose path the stack holds up to lvl_valid)
+    int lvl_valid = 0;
     stk[0] = 0;
-    int qp[3] = {q[0], q[1], q[2]};
-    for (int step = 0;; ++step) {
-        // a3: descend from the deepest shared ancestor
-        const unsigned diff = (unsigned)((q[0] ^ qp[0]) | (q[1] ^ qp[1]) | (q[2] ^ qp[2]));
+    auto descend = [&](const int nq[3], const int pq[3], int &leaf, int &cell_lvl) {
+        const unsigned diff = (unsigned)((nq[0] ^ pq[0]) | (nq[1] ^ pq[1]) | (nq[2] ^ pq[2]));
         const int lc = diff ? D - 32 + __clz(diff) : D - 1;  // level of the common ancestor
         int l = min(lc, lvl_valid);
         int node = stk[l * kBlock];
-        int leaf = -1, cell_lvl = D;
+        leaf = -1;
+        cell_lvl = D;
         for (; l < D; ++l) {
             const int b = D - 1 - l;
-            const int s = (((q[0] >> b) & 1) << 2) | (((q[1] >> b) & 1) << 1) | ((q[2] >> b) & 1);
+            const int s = (((nq[0] >> b) & 1) << 2) | (((nq[1] >> b) & 1) << 1) | ((nq[2] >> b) & 1);
             const int c = __ldg(p.child + (int64_t)node * 8 + s);
             if (c > 0 && l < D - 1) {
                 node = c;
@@ -107,8 +110,19 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
             break;
         }
         lvl_valid = min(l, D - 1);
+    };
 
-        // a4: exit of the cell
+    int leaf, cell_lvl;
+    descend(q, q, leaf, cell_lvl);
+    if (leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
+
+    // exit plane (voxel index) and crossing time per axis, recomputed only
+    // when the plane changes (once per step inside runs of leaves)
+    int kx[3] = {-0x40000000, -0x40000000, -0x40000000};
+    df tcx[3];
+    df t = tin;
+    for (int step = 0;; ++step) {
+        // a4: exit of the current cell
         const int sz = 1 << (D - cell_lvl);
         int qb[3];
         df texit = {__int_as_float(0x7f800000), 0.f};
@@ -118,9 +132,12 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
             qb[a] = q[a] & ~(sz - 1);
             if (d[a] != 0.f) {
                 const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
-                const df tb = cross_time(k, h, Ahi[a], Alo[a], d[a], rd[a]);
-                if (df_lt(tb, texit)) {
-                    texit = tb;
+                if (k != kx[a]) {
+                    kx[a] = k;
+                    tcx[a] = cross_time(k, h, Ahi[a], Alo[a], d[a], rd[a]);
+                }
+                if (df_lt(tcx[a], texit)) {
+                    texit = tcx[a];
                     ax = a;
                 }
             }
@@ -129,13 +146,46 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
         const df tend = last ? tout : texit;
         const float dt = df_sub(tend, t);
 
+        // next voxel and its cell, fetched ahead of shading the current leaf:
+        // the exit axis steps one cell; the other axes are located at t_exit
+        // within the current cell's face (a one-voxel cell keeps them) and
+        // never move backwards
+        bool stop = last;
+        int nq[3] = {q[0], q[1], q[2]};
+        int nleaf = -1, nlvl = D;
+        if (!last) {
+            if (step >= p.step_cap) {
+                atomicOr(p.err, 1u);
+                stop = true;
+            } else {
+                bool outside = false;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a == ax) {
+                        nq[a] = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
+                        outside = nq[a] < 0 || nq[a] >= R;
+                    } else if (sz > 1 && d[a] != 0.f) {
+                        int v = locate_axis(texit, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+                        v = min(max(v, qb[a]), qb[a] + sz - 1);
+                        nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
+                    }
+                }
+                if (outside) {
+                    stop = true;
+                } else {
+                    descend(nq, q, nleaf, nlvl);
+                    if (nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
+                }
+            }
+        }
+
         if (leaf >= 0 && dt > 0.f) {
             // a5..a7
             const float delta = dt * len;
             const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
             float x[3];
             leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
-            const float e = expf(-sig * delta);
+            const float e = __expf(-sig * delta);   // transmittance of the segment
             const float w = Tr * (1.f - e);
 #pragma unroll
             for (int c = 0; c < 3; ++c) col[c] = fmaf(w, sigmoidf_(x[c]), col[c]);
@@ -146,38 +196,17 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
             }
             if (Tr < p.gamma) break;  // a8 early stop (gamma = 0 never stops)
         }
-        if (last) break;
-        if (step >= p.step_cap) {
-            atomicOr(p.err, 1u);
-            break;
-        }
-        // next voxel: the exit axis steps by one cell; the other axes are
-        // located at t_exit within the current cell's face, never backwards
-        int nq[3];
+        if (stop) break;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a == ax) {
-                nq[a] = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
-            } else if (d[a] == 0.f) {
-                nq[a] = q[a];
-            } else {
-                int v = locate_axis(texit, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
-                v = min(max(v, qb[a]), qb[a] + sz - 1);
-                nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
-            }
-        }
-        if (nq[ax] < 0 || nq[ax] >= R) break;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            qp[a] = q[a];
-            q[a] = nq[a];
-        }
+        for (int a = 0; a < 3; ++a) q[a] = nq[a];
+        leaf = nleaf;
+        cell_lvl = nlvl;
         if (df_lt(t, texit)) t = texit;
     }
 }
 
 template <int K, typename T, bool CAMS, bool COUNT>
-__global__ void __launch_bounds__(kBlock) render_kernel(const RenderParams p)
+__global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(const RenderParams p)
 {
     __shared__ int32_t stk_sh[kMaxDepth][kBlock];
     int32_t *stk = &stk_sh[0][threadIdx.x];
