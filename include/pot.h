@@ -182,6 +182,62 @@ pot_status pot_render(const pot_tree *tree, const pot_camera *cams, int32_t n_ca
 pot_status pot_render_rays(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
                            const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
 
+/* ------------------------------------------------------------- backward ---
+ * App. B.3.2: gradients of L = sum_rays <grad_rgb, C> with respect to the
+ * stored leaf values, for the rays of pot_render_rays with the same opts:
+ *   dC/dk_{i,k}  = w_i c_i (1 - c_i) Y_k            (per channel)
+ *   dC/dsigma_i  = delta_i [ c_i T_{i+1} - (C - sum_{j<=i} w_j c_j) ]
+ * (zero where the stored sigma <= 0), summed over channels, rays and segments.
+ * rgb_fwd is the forward colour C of each ray (pot_render_rays output, same
+ * tree and opts); NULL makes the kernel recompute it in a first pass.
+ * ACCUMULATES (+=) into grad_sigma [n_leaves] and grad_sh [n_leaves][K][3]
+ * (float32, canonical layout); the caller zeroes them.  All arrays in device
+ * memory.  Summation order of the float atomics is not deterministic.      */
+pot_status pot_render_backward(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
+                               const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
+                               float *grad_sigma, float *grad_sh, pot_stream stream);
+
+/* ----------------------------------------------------------------- step ---
+ * Sec. 3.3 / App. C: gradient step on the leaf values with the structure
+ * fixed (the paper uses SGD; RMSprop and Adam are offered too), in place on a
+ * float32 tree (other dtypes: POT_ERR_UNSUPPORTED).  Element-wise, separate
+ * learning rates for sigma and SH:
+ *   SGD      x -= lr g
+ *   RMSprop  v = alpha v + (1 - alpha) g^2;  x -= lr g / (sqrt(v) + eps)
+ *   Adam     m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *            x -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps)
+ * (the torch.optim definitions).  state: caller-owned float32 device buffer of
+ * pot_step_state_floats(tree, kind) floats, zero before the first step;
+ * layout [sigma part n_leaves][SH part n_leaves*3K] (Adam: m then v).     */
+typedef enum pot_optimizer { POT_SGD = 0, POT_RMSPROP = 1, POT_ADAM = 2 } pot_optimizer;
+
+typedef struct pot_step_desc {
+    int32_t kind;            /* pot_optimizer */
+    float lr_sigma, lr_sh;
+    float alpha;             /* RMSprop smoothing, e.g. 0.99 */
+    float beta1, beta2;      /* Adam, e.g. 0.9, 0.999 */
+    float eps;               /* e.g. 1e-8 */
+    int32_t step;            /* Adam: 1 for the first step */
+} pot_step_desc;
+
+int64_t pot_step_state_floats(const pot_tree *tree, int32_t kind);
+pot_status pot_step(pot_tree *tree, const pot_step_desc *desc, const float *grad_sigma, const float *grad_sh,
+                    float *state, pot_stream stream);
+
+/* Sec. 3, NeRF loss, as a mean: loss = (1/(3n)) sum (rgb - target)^2 and
+ * grad_rgb = 2 (rgb - target) / (3n) (grad_rgb may be NULL).  rgb, target,
+ * grad_rgb [n][3]; loss: one float; all device memory.                    */
+pot_status pot_loss_mse(int64_t n, const float *rgb, const float *target, float *grad_rgb, float *loss,
+                        pot_stream stream);
+
+/* Pixel rays of cameras (the camera expression above): for k < n, pixel
+ * index pixels[k] = cam * H * W + row * W + col (pixels NULL: k itself), into
+ * origins / dirs [n][3].  cams in host memory (same width/height); pixels,
+ * origins, dirs in device memory.  An index outside the cameras gives
+ * POT_ERR_INVALID_ARG (checked after the launch; synchronises).           */
+pot_status pot_camera_rays(const pot_camera *cams, int32_t n_cams, int64_t n, const int64_t *pixels,
+                           float *origins, float *dirs, pot_stream stream);
+
 /* pot_render for callers that may not allocate GPU memory (the paper has no
  * counterpart; this is a deployment variant).  Applications that embed the
  * renderer and own all GPU memory -- a viewer on a fixed memory budget, a host

@@ -50,6 +50,14 @@ class RenderOpts(C.Structure):
                 ("leaf_touched", C.c_void_p)]
 
 
+class StepDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lr_sigma", C.c_float), ("lr_sh", C.c_float), ("alpha", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("step", C.c_int32)]
+
+
+OPTIMIZERS = {"sgd": 0, "rmsprop": 1, "adam": 2}
+
+
 class TreeInfo(C.Structure):
     _fields_ = [("depth", C.c_int32), ("sh_degree", C.c_int32), ("sh_dim", C.c_int32),
                 ("leaf_dtype", C.c_int32), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
@@ -75,6 +83,10 @@ _SIGS = {
     "pot_render": [_p, _p, C.c_int32, _p, _p, _p, _p],
     "pot_render_rays": [_p, C.c_int64, _p, _p, _p, _p, _p, _p],
     "pot_check": [_p],
+    "pot_render_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p],
+    "pot_step": [_p, _p, _p, _p, _p, _p],
+    "pot_loss_mse": [C.c_int64, _p, _p, _p, _p, _p],
+    "pot_camera_rays": [_p, C.c_int32, C.c_int64, _p, _p, _p, _p],
 }
 
 
@@ -95,6 +107,8 @@ def lib():
             L.pot_last_error.argtypes = []
             L.pot_version.restype = C.c_int32
             L.pot_launch_count.restype = C.c_int64
+            L.pot_step_state_floats.restype = C.c_int64
+            L.pot_step_state_floats.argtypes = [_p, C.c_int32]
             _lib = L
     return _lib
 
@@ -312,3 +326,120 @@ def render_rays(tree: Tree, origins, dirs, rgb=None, t_final=None, bg=(0.0, 0.0,
 def check(stream=None):
     """``pot_check``: synchronise and raise on a device-side traversal error."""
     _check(lib().pot_check(_stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# differentiation and optimisation (App. B.3, Sec. 3.3)
+# ----------------------------------------------------------------------------
+
+def render_backward(tree: Tree, origins, dirs, grad_rgb, rgb_fwd=None, grad_sigma=None, grad_sh=None,
+                    bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0, far=3.0e38, stream=None):
+    """``pot_render_backward``: accumulates into (and returns) grad_sigma [L], grad_sh [L, K, 3]."""
+    import torch
+    inf = tree.info()
+    L, K = inf["n_leaves"], inf["sh_dim"]
+    dev = origins.device
+    if grad_sigma is None:
+        grad_sigma = torch.zeros(L, dtype=torch.float32, device=dev)
+    if grad_sh is None:
+        grad_sh = torch.zeros((L, K, 3), dtype=torch.float32, device=dev)
+    o = _opts(bg, gamma, near, far)
+    _check(lib().pot_render_backward(tree.handle, int(origins.shape[0]), _ptr(origins), _ptr(dirs), _ptr(grad_rgb),
+                                     _ptr(rgb_fwd), C.byref(o), _ptr(grad_sigma), _ptr(grad_sh), _stream(stream)))
+    return grad_sigma, grad_sh
+
+
+def step_state_floats(tree: Tree, kind: str) -> int:
+    return int(lib().pot_step_state_floats(tree.handle, OPTIMIZERS[kind]))
+
+
+def step(tree: Tree, grad_sigma, grad_sh, state=None, kind="rmsprop", lr_sigma=1e-2, lr_sh=1e-2, alpha=0.99,
+         beta1=0.9, beta2=0.999, eps=1e-8, step_index=1, stream=None):
+    """``pot_step``: one optimiser step on the tree's leaf values (float32 trees)."""
+    d = StepDesc(OPTIMIZERS[kind], lr_sigma, lr_sh, alpha, beta1, beta2, eps, step_index)
+    _check(lib().pot_step(tree.handle, C.byref(d), _ptr(grad_sigma), _ptr(grad_sh), _ptr(state), _stream(stream)))
+
+
+def loss_mse(rgb, target, grad=None, want_grad=True, stream=None):
+    """``pot_loss_mse``: (loss [1] tensor, grad [n,3] or None)."""
+    import torch
+    n = int(rgb.shape[0])
+    loss = torch.empty(1, dtype=torch.float32, device=rgb.device)
+    if want_grad and grad is None:
+        grad = torch.empty_like(rgb)
+    _check(lib().pot_loss_mse(n, _ptr(rgb), _ptr(target), _ptr(grad if want_grad else None), _ptr(loss),
+                              _stream(stream)))
+    return loss, grad
+
+
+def camera_rays(cams, pixels=None, n=None, device="cuda", stream=None):
+    """``pot_camera_rays``: (origins, dirs) [n,3] for global pixel indices (int64 tensor) or all pixels."""
+    import torch
+    carr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    if pixels is not None:
+        n = int(pixels.shape[0])
+        device = pixels.device
+    elif n is None:
+        n = len(carr) * carr[0].width * carr[0].height
+    o = torch.empty((n, 3), dtype=torch.float32, device=device)
+    d = torch.empty((n, 3), dtype=torch.float32, device=device)
+    _check(lib().pot_camera_rays(carr, len(carr), n, _ptr(pixels), _ptr(o), _ptr(d), _stream(stream)))
+    return o, d
+
+
+def _autograd_fn():
+    import torch
+
+    class RenderRaysFn(torch.autograd.Function):
+        """rgb = render(tree, rays); gradients flow to two placeholder tensors
+        standing for the tree's sigma [L] and SH [L,K,3] (their values are the
+        tree's; the tree itself is updated by ``step`` or ``Tree.set_values``)."""
+
+        @staticmethod
+        def forward(ctx, sigma_param, sh_param, tree, origins, dirs, bg, gamma, near, far):
+            rgb = render_rays(tree, origins, dirs, bg=bg, gamma=gamma, near=near, far=far)
+            ctx.save_for_backward(origins, dirs, rgb)
+            ctx.tree = tree
+            ctx.cfg = (bg, gamma, near, far)
+            ctx.shapes = (sigma_param.shape, sh_param.shape)
+            return rgb
+
+        @staticmethod
+        def backward(ctx, grad_rgb):
+            o, d, rgb = ctx.saved_tensors
+            bg, gamma, near, far = ctx.cfg
+            gs, gh = render_backward(ctx.tree, o, d, grad_rgb.contiguous(), rgb_fwd=rgb, bg=bg, gamma=gamma,
+                                     near=near, far=far)
+            return gs.reshape(ctx.shapes[0]), gh.reshape(ctx.shapes[1]), None, None, None, None, None, None, None
+
+    return RenderRaysFn
+
+
+_RenderRaysFn = None
+
+
+def render_rays_diff(tree: Tree, sigma_param, sh_param, origins, dirs, bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0,
+                     far=3.0e38):
+    """Differentiable ``render_rays`` (torch.autograd.Function around pot_render_rays / pot_render_backward)."""
+    global _RenderRaysFn
+    if _RenderRaysFn is None:
+        _RenderRaysFn = _autograd_fn()
+    return _RenderRaysFn.apply(sigma_param, sh_param, tree, origins, dirs, tuple(bg), float(gamma), float(near),
+                               float(far))
+
+
+class LeafOptimizer:
+    """Owns the optimiser state of ``pot_step`` for one float32 tree."""
+
+    def __init__(self, tree: Tree, kind="rmsprop", lr_sigma=1e-2, lr_sh=1e-2, alpha=0.99, beta1=0.9, beta2=0.999,
+                 eps=1e-8):
+        import torch
+        self.tree, self.kind = tree, kind
+        self.hp = dict(lr_sigma=lr_sigma, lr_sh=lr_sh, alpha=alpha, beta1=beta1, beta2=beta2, eps=eps)
+        nst = step_state_floats(tree, kind)
+        self.state = torch.zeros(max(nst, 1), dtype=torch.float32, device="cuda")
+        self.t = 0
+
+    def step(self, grad_sigma, grad_sh, stream=None):
+        self.t += 1
+        step(self.tree, grad_sigma, grad_sh, self.state, self.kind, step_index=self.t, stream=stream, **self.hp)

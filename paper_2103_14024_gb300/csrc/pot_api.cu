@@ -564,6 +564,116 @@ pot_status pot_render_rays(const pot_tree *t, int64_t n, const float *origins, c
     return POT_OK;
 }
 
+pot_status pot_render_backward(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
+                               const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
+                               float *grad_sigma, float *grad_sh, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
+    if (n == 0 || t->n_leaves == 0) return POT_OK;
+    if (!origins || !dirs || !grad_rgb || !grad_sigma || !grad_sh)
+        return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(origins) || !is_device_ptr(dirs) || !is_device_ptr(grad_rgb) ||
+        !is_device_ptr(grad_sigma) || !is_device_ptr(grad_sh) || (rgb_fwd && !is_device_ptr(rgb_fwd)))
+        return fail(POT_ERR_INVALID_ARG, "pot_render_backward takes device arrays only");
+    pot_status st = check_opts(opts);
+    if (st != POT_OK) return st;
+    if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
+    const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
+    if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp scratch;
+    POT_CUDA(scratch.alloc(sizeof(unsigned long long), s), "alloc scratch");
+    POT_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), s), "memset");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.ray_o = origins;
+    p.ray_d = dirs;
+    p.n_rays = n;
+    p.near = near;
+    p.far = far;
+    p.n_tiles = (n + 31) / 32;
+    p.tile_counter = static_cast<unsigned long long *>(scratch.p);
+    POT_CUDA(launch_backward(p, grad_rgb, rgb_fwd, grad_sigma, grad_sh, t->desc.leaf_dtype, t->K, s), "backward");
+    return POT_OK;
+}
+
+int64_t pot_step_state_floats(const pot_tree *t, int32_t kind)
+{
+    if (!t) return -1;
+    const int64_t per = t->n_leaves * (1 + 3 * (int64_t)t->K);
+    if (kind == POT_SGD) return 0;
+    if (kind == POT_RMSPROP) return per;
+    if (kind == POT_ADAM) return 2 * per;
+    return -1;
+}
+
+pot_status pot_step(pot_tree *t, const pot_step_desc *d, const float *grad_sigma, const float *grad_sh, float *state,
+                    pot_stream stream)
+{
+    if (!t || !d) return fail(POT_ERR_INVALID_ARG, "NULL tree or desc");
+    if (t->desc.leaf_dtype != POT_F32) return fail(POT_ERR_UNSUPPORTED, "pot_step needs a float32 tree");
+    if (d->kind < POT_SGD || d->kind > POT_ADAM) return fail(POT_ERR_INVALID_ARG, "unknown optimiser kind");
+    if (!std::isfinite(d->lr_sigma) || !std::isfinite(d->lr_sh) || !std::isfinite(d->eps))
+        return fail(POT_ERR_INVALID_ARG, "learning rates and eps must be finite");
+    if (d->kind == POT_ADAM && d->step < 1) return fail(POT_ERR_INVALID_ARG, "Adam step counts from 1");
+    if (t->n_leaves == 0) return POT_OK;
+    if (!grad_sigma || !grad_sh || (d->kind != POT_SGD && !state)) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(grad_sigma) || !is_device_ptr(grad_sh) || (state && !is_device_ptr(state)))
+        return fail(POT_ERR_INVALID_ARG, "pot_step takes device arrays only");
+    DeviceGuard g(t->device);
+    POT_CUDA(launch_step(t, d->kind, d->lr_sigma, d->lr_sh, d->alpha, d->beta1, d->beta2, d->eps, d->step, grad_sigma,
+                         grad_sh, state, (cudaStream_t)stream),
+             "step");
+    return POT_OK;
+}
+
+pot_status pot_loss_mse(int64_t n, const float *rgb, const float *target, float *grad_rgb, float *loss,
+                        pot_stream stream)
+{
+    if (n < 0 || !loss) return fail(POT_ERR_INVALID_ARG, "bad n or NULL loss");
+    if (n > 0 && (!rgb || !target)) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(loss) || (n > 0 && (!is_device_ptr(rgb) || !is_device_ptr(target))) ||
+        (grad_rgb && !is_device_ptr(grad_rgb)))
+        return fail(POT_ERR_INVALID_ARG, "pot_loss_mse takes device arrays only");
+    POT_CUDA(launch_mse(n, rgb, target, grad_rgb, loss, (cudaStream_t)stream), "loss");
+    return POT_OK;
+}
+
+pot_status pot_camera_rays(const pot_camera *cams, int32_t n_cams, int64_t n, const int64_t *pixels, float *origins,
+                           float *dirs, pot_stream stream)
+{
+    if (n_cams <= 0 || !cams || n < 0) return fail(POT_ERR_INVALID_ARG, "bad cameras or n");
+    if (n == 0) return POT_OK;
+    if (is_device_ptr(cams)) return fail(POT_ERR_INVALID_ARG, "cams must be in host memory");
+    if (!origins || !dirs || !is_device_ptr(origins) || !is_device_ptr(dirs) || (pixels && !is_device_ptr(pixels)))
+        return fail(POT_ERR_INVALID_ARG, "pixels / origins / dirs must be device memory");
+    const int W = cams[0].width, H = cams[0].height;
+    for (int c = 0; c < n_cams; ++c)
+        if (cams[c].width != W || cams[c].height != H || W <= 0 || H <= 0)
+            return fail(POT_ERR_INVALID_ARG, "cameras must share a positive width and height");
+    if (!pixels && n > (int64_t)n_cams * W * H) return fail(POT_ERR_INVALID_ARG, "n exceeds the cameras' pixels");
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp scratch;
+    const size_t cam_off = 256;
+    POT_CUDA(scratch.alloc(cam_off + sizeof(pot_camera) * n_cams, s), "alloc scratch");
+    char *sp = static_cast<char *>(scratch.p);
+    POT_CUDA(cudaMemsetAsync(sp, 0, sizeof(unsigned), s), "memset");
+    POT_CUDA(cudaMemcpyAsync(sp + cam_off, cams, sizeof(pot_camera) * n_cams, cudaMemcpyHostToDevice, s), "copy cams");
+    POT_CUDA(launch_camera_rays(reinterpret_cast<const pot_camera *>(sp + cam_off), n_cams, W, H, n, pixels, origins,
+                                dirs, reinterpret_cast<unsigned *>(sp), s),
+             "camera rays");
+    if (pixels) {
+        unsigned flag = 0;
+        POT_CUDA(cudaMemcpyAsync(&flag, sp, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "copy flag");
+        POT_CUDA(cudaStreamSynchronize(s), "sync");
+        if (flag) return fail(POT_ERR_INVALID_ARG, "a pixel index lies outside the cameras");
+    }
+    return POT_OK;
+}
+
 pot_status pot_check(pot_stream stream)
 {
     cudaStream_t s = (cudaStream_t)stream;

@@ -1,0 +1,328 @@
+// pot_backward.cu -- analytic derivatives of the render (App. B.3.2), the
+// optimiser step on the leaves (Sec. 3.3), the MSE loss of a ray batch (Sec. 3,
+// NeRF loss) and pixel-ray generation for training batches.
+//
+// Backward, per ray (replaying the forward walk, so segments and the early-
+// stop point are the forward's):
+//   c_i = S(x_i),  x_i = sum_k k_{i,k} Y_k,  w_i = T_i (1 - e^{-sigma_i delta_i})
+//   dC/dx_i      = w_i c_i (1 - c_i)                         (colour derivative, chain rule)
+//   dC/dk_{i,k}  = dC/dx_i Y_k                               (basis constant along the ray)
+//   dC/dsigma_i  = delta_i [ c_i T_{i+1} - S_i ],  S_i = sum_{k>i} w_k c_k + T_N bg
+//                = delta_i [ c_i T_{i+1} - (C - sum_{k<=i} w_k c_k) ]
+// i.e. the paper's two passes: the composited colour C (the forward output,
+// or a first in-kernel pass) minus a running prefix.  Zero for sigma <= 0.
+// Gradients of L = sum_rays <dL/dC, C> are scattered with float reductions
+// (16-byte vector reductions where the row allows).
+#include <cmath>
+
+#include "pot_render.cuh"
+
+namespace pot {
+
+namespace {
+
+__device__ __forceinline__ void red_add(float *a, float v)
+{
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(a), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add4(float *a, float x, float y, float z, float w)
+{
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(x), "f"(y), "f"(z),
+                 "f"(w)
+                 : "memory");
+}
+
+template <int K, typename T>
+struct GradVisitor {
+    const T *sig_arr;
+    const T *sh_arr;
+    float gamma;
+    float g[3];       // dL/dC of the ray
+    float ctot[3];    // C of the ray (background included)
+    float prefix[3];  // sum over composited segments of w c
+    float Tr;
+    float *grad_sigma;
+    float *grad_sh;
+    __device__ __forceinline__ bool operator()(int leaf, float delta, const float *Y)
+    {
+        const float sraw = Store<T>::load_sigma(sig_arr, leaf);
+        const float sig = fmaxf(sraw, 0.f);
+        float x[3];
+        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
+        const float e = __expf(-sig * delta);  // same operations as the forward
+        const float w = Tr * (1.f - e);
+        const float Tn = Tr * e;
+        float gx[3], gs = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float col = sigmoidf_(x[c]);
+            prefix[c] = fmaf(w, col, prefix[c]);
+            gx[c] = g[c] * w * col * (1.f - col);
+            gs = fmaf(g[c], fmaf(col, Tn, -(ctot[c] - prefix[c])), gs);
+        }
+        float *row = grad_sh + (int64_t)leaf * (3 * K);
+        if ((3 * K) % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < 3 * K; j += 4)
+                red_add4(row + j, gx[j % 3] * Y[j / 3], gx[(j + 1) % 3] * Y[(j + 1) / 3],
+                         gx[(j + 2) % 3] * Y[(j + 2) / 3], gx[(j + 3) % 3] * Y[(j + 3) / 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3 * K; ++j) red_add(row + j, gx[j % 3] * Y[j / 3]);
+        }
+        if (sraw > 0.f) red_add(grad_sigma + leaf, gs * delta);
+        Tr = Tn;
+        return Tr < gamma;
+    }
+};
+
+struct BackwardParams {
+    RenderParams r;
+    const float *grad_rgb;
+    const float *rgb_fwd;  // NULL: computed by a first pass
+    float *grad_sigma;
+    float *grad_sh;
+};
+
+template <int K, typename T, bool HAVE_FWD>
+__global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) backward_kernel(const BackwardParams bp)
+{
+    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
+    int32_t *stk = &stk_sh[0][threadIdx.x];
+    const RenderParams &p = bp.r;
+    const int lane = threadIdx.x & 31;
+    const T *sig_arr = static_cast<const T *>(p.sigma);
+    const T *sh_arr = static_cast<const T *>(p.sh);
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1ull);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= (unsigned long long)p.n_tiles) break;
+        const int64_t ray = (int64_t)tile * 32 + lane;
+        if (ray < p.n_rays) {
+            float o[3], d[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                o[r] = __ldg(p.ray_o + 3 * ray + r);
+                d[r] = __ldg(p.ray_d + 3 * ray + r);
+            }
+            GradVisitor<K, T> gv;
+            gv.sig_arr = sig_arr;
+            gv.sh_arr = sh_arr;
+            gv.gamma = p.gamma;
+            gv.Tr = 1.f;
+            gv.grad_sigma = bp.grad_sigma;
+            gv.grad_sh = bp.grad_sh;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                gv.g[c] = __ldg(bp.grad_rgb + 3 * ray + c);
+                gv.prefix[c] = 0.f;
+            }
+            if (HAVE_FWD) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(bp.rgb_fwd + 3 * ray + c);
+            } else {
+                ShadeVisitor<K, T, false> sv{sig_arr, sh_arr, nullptr, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, p.near, p.far, sv);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gv.ctot[c] = fmaf(sv.Tr, p.bg[c], sv.col[c]);
+            }
+            if (gv.g[0] != 0.f || gv.g[1] != 0.f || gv.g[2] != 0.f)
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, p.near, p.far, gv);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_backward_t(const BackwardParams &bp, int K, bool have_fwd, cudaStream_t s)
+{
+    using Fn = void (*)(const BackwardParams);
+    Fn fn = nullptr;
+#define POT_PICK(KK) \
+    if (K == KK) fn = have_fwd ? backward_kernel<KK, T, true> : backward_kernel<KK, T, false>;
+    POT_PICK(1)
+    POT_PICK(4)
+    POT_PICK(9)
+    POT_PICK(16)
+#undef POT_PICK
+    if (!fn) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (bp.r.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    fn<<<(unsigned)blocks, kBlock, 0, s>>>(bp);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---- optimiser step on the leaves ------------------------------------------
+struct StepParams {
+    int64_t L;
+    int K3;      // 3K
+    int stride;  // SH record stride (elements)
+    float lr_sigma, lr_sh, alpha, beta1, beta2, eps;
+    float bc1, bc2;  // Adam bias corrections 1 - beta^t
+};
+
+template <int KIND>
+__global__ void k_step(StepParams sp, float *sigma, float *sh, const float *gs, const float *gsh, float *state)
+{
+    const int64_t N = sp.L * (1 + sp.K3);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        float *param;
+        float g, lr;
+        if (j < sp.L) {
+            param = sigma + j;
+            g = gs[j];
+            lr = sp.lr_sigma;
+        } else {
+            const int64_t jj = j - sp.L;
+            const int64_t i = jj / sp.K3;
+            param = sh + i * sp.stride + (jj - i * sp.K3);
+            g = gsh[jj];
+            lr = sp.lr_sh;
+        }
+        float x = *param;
+        if (KIND == POT_SGD) {
+            x -= lr * g;
+        } else if (KIND == POT_RMSPROP) {
+            float v = state[j];
+            v = sp.alpha * v + (1.f - sp.alpha) * g * g;
+            state[j] = v;
+            x -= lr * g / (sqrtf(v) + sp.eps);
+        } else {
+            float m = state[j], v = state[N + j];
+            m = sp.beta1 * m + (1.f - sp.beta1) * g;
+            v = sp.beta2 * v + (1.f - sp.beta2) * g * g;
+            state[j] = m;
+            state[N + j] = v;
+            x -= (lr / sp.bc1) * m / (sqrtf(v) / sqrtf(sp.bc2) + sp.eps);
+        }
+        *param = x;
+    }
+}
+
+// ---- MSE loss of a ray batch: L = mean over n*3 of (rgb - target)^2 --------
+__global__ void k_mse(int64_t n3, const float *rgb, const float *target, float *grad, float *loss)
+{
+    __shared__ float part[kBlock / 32];
+    const float scale = 2.f / (float)n3;
+    float acc = 0.f;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n3; j += (int64_t)gridDim.x * blockDim.x) {
+        const float r = rgb[j] - target[j];
+        acc = fmaf(r, r, acc);
+        if (grad) grad[j] = scale * r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < kBlock / 32; ++w) s += part[w];
+        atomicAdd(loss, s / (float)n3);
+    }
+}
+
+// ---- pixel rays (the camera expression of the public header) ----------------
+__global__ void k_camera_rays(const pot_camera *cams, int n_cams, int64_t per_cam, int W, int64_t n,
+                              const int64_t *pixels, float *o, float *d)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = pixels ? pixels[k] : k;
+        int64_t cam = pix / per_cam;
+        if (cam < 0 || cam >= n_cams) cam = cam < 0 ? 0 : n_cams - 1;  // guarded by the host check
+        const int64_t rem = pix - cam * per_cam;
+        const int j = (int)(rem / W), i = (int)(rem - (int64_t)j * W);
+        const pot_camera *c = cams + cam;
+        const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), c->cx), c->fx);
+        const float yc = -__fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), c->cy), c->fy);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            d[3 * k + r] = __fsub_rn(__fadd_rn(__fmul_rn(c->c2w[r][0], xc), __fmul_rn(c->c2w[r][1], yc)),
+                                     c->c2w[r][2]);
+            o[3 * k + r] = c->c2w[r][3];
+        }
+    }
+}
+
+__global__ void k_pixel_range(int64_t n, const int64_t *pixels, int64_t total, unsigned *flag)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (pixels[k] < 0 || pixels[k] >= total) atomicOr(flag, 1u);
+}
+
+unsigned grid_n(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const RenderParams &r, const float *grad_rgb, const float *rgb_fwd, float *grad_sigma,
+                            float *grad_sh, int dtype, int K, cudaStream_t s)
+{
+    BackwardParams bp{r, grad_rgb, rgb_fwd, grad_sigma, grad_sh};
+    switch (dtype) {
+    case POT_F32: return launch_backward_t<float>(bp, K, rgb_fwd != nullptr, s);
+    case POT_F16: return launch_backward_t<__half>(bp, K, rgb_fwd != nullptr, s);
+    default: return launch_backward_t<__nv_bfloat16>(bp, K, rgb_fwd != nullptr, s);
+    }
+}
+
+cudaError_t launch_step(pot_tree *t, int kind, float lr_sigma, float lr_sh, float alpha, float beta1, float beta2,
+                        float eps, int step, const float *gs, const float *gsh, float *state, cudaStream_t s)
+{
+    StepParams sp;
+    sp.L = t->n_leaves;
+    sp.K3 = 3 * t->K;
+    sp.stride = t->stride;
+    sp.lr_sigma = lr_sigma;
+    sp.lr_sh = lr_sh;
+    sp.alpha = alpha;
+    sp.beta1 = beta1;
+    sp.beta2 = beta2;
+    sp.eps = eps;
+    sp.bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+    sp.bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+    if (sp.L == 0) return cudaSuccess;
+    const unsigned g = grid_n(sp.L * (1 + sp.K3));
+    float *sig = static_cast<float *>(t->sigma);
+    float *sh = static_cast<float *>(t->sh);
+    if (kind == POT_SGD) k_step<POT_SGD><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
+    else if (kind == POT_RMSPROP) k_step<POT_RMSPROP><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
+    else k_step<POT_ADAM><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse(int64_t n, const float *rgb, const float *target, float *grad, float *loss, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
+    if (e != cudaSuccess || n == 0) return e;
+    k_mse<<<grid_n(3 * n), kBlock, 0, s>>>(3 * n, rgb, target, grad, loss);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int H, int64_t n, const int64_t *pixels,
+                               float *o, float *d, unsigned *d_flag, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (pixels) {
+        k_pixel_range<<<grid_n(n), 256, 0, s>>>(n, pixels, (int64_t)n_cams * W * H, d_flag);
+        count_launch();
+    }
+    k_camera_rays<<<grid_n(n), 256, 0, s>>>(d_cams, n_cams, (int64_t)W * H, W, n, pixels, o, d);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pot

@@ -81,6 +81,14 @@ cudaError_t export_leaves(const pot_tree *t, float *d_sigma, float *d_sh, cudaSt
 cudaError_t launch_query(const pot_tree *t, int64_t n, const float *xyz, int32_t *out, cudaStream_t s);
 cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaStream_t s);
 
+cudaError_t launch_backward(const RenderParams &r, const float *grad_rgb, const float *rgb_fwd, float *grad_sigma,
+                            float *grad_sh, int dtype, int K, cudaStream_t s);
+cudaError_t launch_step(pot_tree *t, int kind, float lr_sigma, float lr_sh, float alpha, float beta1, float beta2,
+                        float eps, int step, const float *gs, const float *gsh, float *state, cudaStream_t s);
+cudaError_t launch_mse(int64_t n, const float *rgb, const float *target, float *grad, float *loss, cudaStream_t s);
+cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int H, int64_t n, const int64_t *pixels,
+                               float *o, float *d, unsigned *d_flag, cudaStream_t s);
+
 unsigned int *device_error_word();   // per-device word raised by kernels
 void set_last_error(const char *msg); // message returned by pot_last_error on this thread
 void count_launch(int n = 1);

@@ -26,10 +26,15 @@ constexpr int kBlock = 256;
 #define POT_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
 #endif
 
-template <int K, typename T, bool COUNT>
-__device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
-                                          int32_t *stk, const float o[3], const float d[3], float near,
-                                          float far, float col[3], float &Tr, int &nseg)
+// Walks one ray through the octree (a2-a4) and calls vis(leaf, delta, Y) for
+// every leaf segment of positive length in order (Y: the SH basis at the ray
+// direction); the walk ends when vis returns true, at the far clip, or when
+// the ray leaves the box.  The next cell is located and its leaf prefetched
+// before vis runs on the current one.
+template <int K, typename T, typename Visitor>
+__device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
+                                         int32_t *stk, const float o[3], const float d[3], float near,
+                                         float far, Visitor &vis)
 {
     const int D = p.depth;
     const int R = p.R;
@@ -180,21 +185,7 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
         }
 
         if (leaf >= 0 && dt > 0.f) {
-            // a5..a7
-            const float delta = dt * len;
-            const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
-            float x[3];
-            leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
-            const float e = __expf(-sig * delta);   // transmittance of the segment
-            const float w = Tr * (1.f - e);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) col[c] = fmaf(w, sigmoidf_(x[c]), col[c]);
-            Tr *= e;
-            if (COUNT) {
-                ++nseg;
-                p.leaf_touched[leaf] = 1;
-            }
-            if (Tr < p.gamma) break;  // a8 early stop (gamma = 0 never stops)
+            if (vis(leaf, dt * len, Y)) break;
         }
         if (stop) break;
 #pragma unroll
@@ -204,6 +195,34 @@ __device__ __forceinline__ void trace_ray(const RenderParams &p, const T *sig_ar
         if (df_lt(t, texit)) t = texit;
     }
 }
+
+// a5-a8 for one leaf segment: fetch, colour, composite, early stop.
+template <int K, typename T, bool COUNT>
+struct ShadeVisitor {
+    const T *sig_arr;
+    const T *sh_arr;
+    uint8_t *touched;
+    float gamma;
+    float col[3];
+    float Tr;
+    int nseg;
+    __device__ __forceinline__ bool operator()(int leaf, float delta, const float *Y)
+    {
+        const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
+        float x[3];
+        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
+        const float e = __expf(-sig * delta);  // transmittance of the segment
+        const float w = Tr * (1.f - e);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) col[c] = fmaf(w, sigmoidf_(x[c]), col[c]);
+        Tr *= e;
+        if (COUNT) {
+            ++nseg;
+            touched[leaf] = 1;
+        }
+        return Tr < gamma;  // a8 early stop (gamma = 0 never stops)
+    }
+};
 
 template <int K, typename T, bool CAMS, bool COUNT>
 __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(const RenderParams p)
@@ -258,14 +277,12 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
             far = p.far;
         }
         if (valid) {
-            float col[3] = {0.f, 0.f, 0.f};
-            float Tr = 1.f;
-            int nseg = 0;
-            trace_ray<K, T, COUNT>(p, sig_arr, sh_arr, stk, o, d, near, far, col, Tr, nseg);
+            ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, near, far, v);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) p.rgb[3 * ray + c] = fmaf(Tr, p.bg[c], col[c]);
-            if (p.t_final) p.t_final[ray] = Tr;
-            if (COUNT) p.seg_count[ray] = nseg;
+            for (int c = 0; c < 3; ++c) p.rgb[3 * ray + c] = fmaf(v.Tr, p.bg[c], v.col[c]);
+            if (p.t_final) p.t_final[ray] = v.Tr;
+            if (COUNT) p.seg_count[ray] = v.nseg;
         }
     }
 }
