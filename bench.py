@@ -213,6 +213,96 @@ def l2_read_peak(torch):
     return 2 * x.numel() * 4 * n / (s.elapsed_time(e) * 1e-3) / 1e9
 
 
+def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
+    """Direct octree optimisation (Sec. 3.3): fit a perturbed copy of the main tree
+    (SH + N(0, 0.3), sigma x U(0.5, 1.5)) to renders of the main tree from 100
+    training views of 800x800 on the upper hemisphere; batches of random rays,
+    MSE, backward, optimiser step.  Reports the backward kernel alone and the
+    whole step in Mrays/s."""
+    cams = synth.cameras_train(n=100)
+    all_o, all_d = pot.camera_rays(cams)
+    target = pot.render_rays(target_tree, all_o, all_d, gamma=GAMMA, near=2.0, far=6.0)
+    tree = pot.Tree.from_scene(synth.perturbed(scene, 1003))
+    info = tree.info()
+    L, K = info["n_leaves"], info["sh_dim"]
+    opt = pot.LeafOptimizer(tree, args.train_opt, lr_sigma=args.train_lr_sigma, lr_sh=args.train_lr_sh)
+    gs = torch.zeros(L, dtype=torch.float32, device="cuda")
+    gh = torch.zeros((L, K, 3), dtype=torch.float32, device="cuda")
+    B = args.train_batch
+    gen = torch.Generator(device="cuda").manual_seed(1003)
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("bwd", "step")}
+    losses, t_bwd, t_step = [], [], []
+    n_total = args.train_steps + 3
+    for it in range(n_total):
+        ev["step"][0].record()
+        idx = torch.randint(0, all_o.shape[0], (B,), device="cuda", generator=gen)
+        o, d, y = all_o[idx], all_d[idx], target[idx]
+        rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
+        loss, g = pot.loss_mse(rgb, y)
+        gs.zero_()
+        gh.zero_()
+        ev["bwd"][0].record()
+        pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0, far=6.0)
+        ev["bwd"][1].record()
+        opt.step(gs, gh)
+        ev["step"][1].record()
+        torch.cuda.synchronize()
+        losses.append(float(loss.item()))
+        if it >= 3:
+            t_bwd.append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
+            t_step.append(ev["step"][0].elapsed_time(ev["step"][1]))
+    pot.check()
+    tree.free()
+    mb, ms = sum(t_bwd) / len(t_bwd), sum(t_step) / len(t_step)
+    return {"workload": "fit a perturbed main tree to 100 training views of 800x800 (hemisphere), MSE",
+            "rays_per_batch": B, "optimizer": args.train_opt, "lr_sigma": args.train_lr_sigma,
+            "lr_sh": args.train_lr_sh, "steps": args.train_steps,
+            "bwd_mrays_s": round(B / (mb * 1e-3) / 1e6, 2), "bwd_ms": round(mb, 4),
+            "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
+            "step_parts": "random batch + gather (torch), forward, MSE, zero grads (torch), backward, optimiser step",
+            "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6)}
+
+
+def serve_measure(pot, torch, synth, args):
+    """Continuous-batching server: 4 resident fp16 trees (depth 7/8/9/10, SH degree
+    1/2/3/3), Poisson arrivals, resolutions from {256^2, 512^2, 800^2, 1920x1080};
+    p50/p99 latency (arrival -> completion event) and rays/s, batched vs one
+    request at a time; plus a burst (all requests at t = 0) for throughput."""
+    import numpy as np
+    from paper_2103_14024_gb300.serve import RenderServer, Request, summarize
+    trees = []
+    for i, (D, deg) in enumerate(synth.SERVE_TREES):
+        sc = synth.scene_shapes_torch(1004 + i, depth=D, sh_degree=deg, device="cuda")
+        trees.append(pot.Tree.build_sparse(D, deg, sc.bbox_lo, sc.bbox_size, sc.morton, sc.sigma, sc.sh,
+                                           dtype="f16"))
+        del sc
+    torch.cuda.empty_cache()
+    resident = sum(t.info()["bytes"] for t in trees)
+    budget = resident + (1 << 30)      # 1 GiB of in-flight outputs on top of the resident trees
+    arrival, tree_idx, cams = synth.serve_requests(1004, args.serve_requests, rate_hz=args.serve_rate)
+    out = {"trees": [{"depth": D, "sh_degree": deg, "leaves": int(t.info()["n_leaves"]),
+                      "bytes": int(t.info()["bytes"])} for (D, deg), t in zip(synth.SERVE_TREES, trees)],
+           "rate_hz": args.serve_rate, "hbm_budget_bytes": int(budget)}
+    # warm the kernels (one launch per tree group) outside the measurement
+    warm = [Request(i, 0.0, int(tree_idx[i]), cams[i]) for i in range(min(8, len(cams)))]
+    RenderServer(trees, budget).run(warm, mode="batch")
+    torch.cuda.synchronize()
+    for label, arr in (("poisson", arrival), ("burst", np.zeros_like(arrival))):
+        for mode in ("batch", "alone"):
+            reqs = [Request(i, float(arr[i]), int(tree_idx[i]), cams[i]) for i in range(len(cams))]
+            srv = RenderServer(trees, budget, streams=3, gamma=GAMMA)
+            t0 = time.perf_counter()
+            srv.run(reqs, mode=mode)
+            torch.cuda.synchronize()
+            out[f"{label}_{mode}"] = summarize(reqs)
+            for r in reqs:
+                r.rgb = None
+    pot.check()
+    for t in trees:
+        t.free()
+    return out
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -242,6 +332,15 @@ def main():
     ap.add_argument("--variants", default="f16,bf16", help="extra leaf dtypes to time ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=30)
+    ap.add_argument("--train-batch", type=int, default=1 << 18)
+    ap.add_argument("--train-opt", default="rmsprop", choices=["sgd", "rmsprop", "adam"])
+    ap.add_argument("--train-lr-sigma", type=float, default=1.0)
+    ap.add_argument("--train-lr-sh", type=float, default=1e-2)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rate", type=float, default=300.0)
     ap.add_argument("--views", type=int, default=N_VIEWS,
                     help="cameras per step (a smaller case for profiler captures; the benchmark uses 200)")
     args = ap.parse_args()
@@ -367,6 +466,10 @@ def main():
         r["tree"].free()
     if variants:
         line["variants"] = variants
+    if not args.no_train:
+        line["train"] = train_measure(pot, torch, synth, scene, main_res["tree"], args, barrier)
+    if not args.no_serve:
+        line["serve"] = serve_measure(pot, torch, synth, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         views = [0, 25, 50, 75, 100, 125, 150, 175]
         rate, n, dt, thr = run_oracle_timing(scene, cams, views, 2)

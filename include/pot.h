@@ -259,6 +259,28 @@ pot_status pot_camera_rays(const pot_camera *cams, int32_t n_cams, int64_t n, co
 pot_status pot_render_noalloc(const pot_tree *tree, const pot_camera *cams, int32_t n_cams,
                               const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
 
+/* ---------------------------------------------------------------- batch ---
+ * Many render requests in one call -- the work list of a continuous-batching
+ * server (the paper's real-time viewer renders one view at a time, Sec. 4.5;
+ * this is its multi-request form).  Each item names its own tree, camera
+ * (any resolution), background, early-stop threshold and outputs; items may
+ * use different trees, SH degrees and leaf dtypes.  Items are grouped by
+ * (SH degree, dtype) and each group is one kernel launch on the stream, whose
+ * warps draw 8x4-pixel tiles from all the group's items.  Per-ray arithmetic
+ * is pot_render's: a request's pixels are identical alone or in a batch.
+ * items: host array; rgb [H][W][3] and t_final [H][W] (may be NULL) in device
+ * memory; trees on the current device.                                    */
+typedef struct pot_render_item {
+    const pot_tree *tree;
+    pot_camera cam;
+    float bg[3];
+    float gamma;
+    float *rgb;
+    float *t_final;
+} pot_render_item;
+
+pot_status pot_render_batch(const pot_render_item *items, int32_t n_items, pot_stream stream);
+
 /* Number of CUDA kernels launched by this library in this process since it
  * was loaded (a counter for benchmarks). */
 int64_t pot_launch_count(void);

@@ -50,6 +50,11 @@ class RenderOpts(C.Structure):
                 ("leaf_touched", C.c_void_p)]
 
 
+class RenderItem(C.Structure):
+    _fields_ = [("tree", C.c_void_p), ("cam", Camera), ("bg", C.c_float * 3), ("gamma", C.c_float),
+                ("rgb", C.c_void_p), ("t_final", C.c_void_p)]
+
+
 class StepDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("lr_sigma", C.c_float), ("lr_sh", C.c_float), ("alpha", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("step", C.c_int32)]
@@ -87,6 +92,7 @@ _SIGS = {
     "pot_step": [_p, _p, _p, _p, _p, _p],
     "pot_loss_mse": [C.c_int64, _p, _p, _p, _p, _p],
     "pot_camera_rays": [_p, C.c_int32, C.c_int64, _p, _p, _p, _p],
+    "pot_render_batch": [_p, C.c_int32, _p],
 }
 
 
@@ -443,3 +449,17 @@ class LeafOptimizer:
     def step(self, grad_sigma, grad_sh, stream=None):
         self.t += 1
         step(self.tree, grad_sigma, grad_sh, self.state, self.kind, step_index=self.t, stream=stream, **self.hp)
+
+
+def render_batch(items, stream=None):
+    """``pot_render_batch``: items = [(tree, camera record, rgb tensor [H,W,3], bg, gamma, t_final or None)]."""
+    arr = (RenderItem * len(items))()
+    for k, (tree, cam, rgb, bg, gamma, tf) in enumerate(items):
+        r = arr[k]
+        r.tree = tree.handle
+        C.memmove(C.byref(r.cam), np.ascontiguousarray(cam).ctypes.data, 80)
+        r.bg[0], r.bg[1], r.bg[2] = bg
+        r.gamma = gamma
+        r.rgb = rgb.data_ptr()
+        r.t_final = None if tf is None else tf.data_ptr()
+    _check(lib().pot_render_batch(arr, len(items), _stream(stream)))

@@ -564,6 +564,34 @@ pot_status pot_render_rays(const pot_tree *t, int64_t n, const float *origins, c
     return POT_OK;
 }
 
+pot_status pot_render_batch(const pot_render_item *items, int32_t n_items, pot_stream stream)
+{
+    if (n_items < 0) return fail(POT_ERR_INVALID_ARG, "n_items < 0");
+    if (n_items == 0) return POT_OK;
+    if (!items) return fail(POT_ERR_INVALID_ARG, "items is NULL");
+    int dev = 0;
+    POT_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    for (int i = 0; i < n_items; ++i) {
+        const pot_render_item &r = items[i];
+        if (!r.tree || r.tree->device != dev) return fail(POT_ERR_INVALID_ARG, "item %d: NULL tree or other device", i);
+        const pot_camera &k = r.cam;
+        bool ok = k.width > 0 && k.height > 0 && (int64_t)k.width * k.height <= (1ll << 31) && std::isfinite(k.fx) &&
+                  std::isfinite(k.fy) && std::isfinite(k.cx) && std::isfinite(k.cy) && k.fx != 0.f && k.fy != 0.f &&
+                  !std::isnan(k.near) && !std::isnan(k.far) && k.near >= 0.f;
+        for (int a = 0; a < 3; ++a)
+            for (int q = 0; q < 4; ++q) ok = ok && std::isfinite(k.c2w[a][q]);
+        for (int c = 0; c < 3; ++c) ok = ok && std::isfinite(r.bg[c]);
+        ok = ok && r.gamma >= 0.f && std::isfinite(r.gamma);
+        if (!ok) return fail(POT_ERR_INVALID_ARG, "item %d: invalid camera, bg or gamma", i);
+        if (!r.rgb || !is_device_ptr(r.rgb) || (r.t_final && !is_device_ptr(r.t_final)))
+            return fail(POT_ERR_INVALID_ARG, "item %d: rgb / t_final must be device memory", i);
+    }
+    unsigned int *err = device_error_word();
+    if (!err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    POT_CUDA(launch_render_batch(items, n_items, (cudaStream_t)stream, err), "render_batch");
+    return POT_OK;
+}
+
 pot_status pot_render_backward(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
                                const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
                                float *grad_sigma, float *grad_sh, pot_stream stream)

@@ -89,6 +89,8 @@ cudaError_t launch_mse(int64_t n, const float *rgb, const float *target, float *
 cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int H, int64_t n, const int64_t *pixels,
                                float *o, float *d, unsigned *d_flag, cudaStream_t s);
 
+cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_t s, unsigned int *err);
+
 unsigned int *device_error_word();   // per-device word raised by kernels
 void set_last_error(const char *msg); // message returned by pot_last_error on this thread
 void count_launch(int n = 1);

@@ -1,0 +1,179 @@
+"""Continuous-batching render server over resident PlenOctrees.
+
+Requests (tree, camera of any resolution, arrival time) enter a wait queue.
+A request is admitted when its output buffer fits the HBM budget left after
+the resident trees and the outputs already in flight; admitted requests are
+packed, as they come, into ``pot_render_batch`` launches (one work list per
+launch, mixed trees and resolutions) on a small ring of CUDA streams, so work
+that arrives while earlier launches run overlaps with them on the device.
+Completion is read from CUDA events; a finished request releases its budget.
+Mode ``alone`` renders one request per launch on one stream, in arrival order
+(the baseline the batching is compared with).
+
+All GPU work runs in libpot kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import render_batch
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the run
+    tree_id: int
+    cam: object             # camera record (80 bytes, synth.CAMERA_DTYPE)
+    out_bytes: int = 0
+    rgb: object = None
+    t_admit: float = -1.0
+    t_launch: float = -1.0
+    t_done: float = -1.0
+    rejected: bool = False
+
+    @property
+    def rays(self) -> int:
+        return int(self.cam["width"]) * int(self.cam["height"])
+
+
+class Admission:
+    """HBM accounting: resident tree bytes + bytes of outputs held by admitted requests."""
+
+    def __init__(self, budget_bytes: int, resident_bytes: int):
+        if resident_bytes > budget_bytes:
+            raise ValueError("resident trees exceed the HBM budget")
+        self.budget = int(budget_bytes)
+        self.resident = int(resident_bytes)
+        self.used = 0
+
+    def fits(self, nbytes: int) -> bool:
+        return self.resident + self.used + nbytes <= self.budget
+
+    def take(self, nbytes: int) -> bool:
+        if not self.fits(nbytes):
+            return False
+        self.used += nbytes
+        return True
+
+    def release(self, nbytes: int) -> None:
+        self.used -= nbytes
+        assert self.used >= 0
+
+
+class RenderServer:
+    def __init__(self, trees, hbm_budget_bytes: int, streams: int = 3, max_rays_per_launch: int = 8 << 20,
+                 bg=(0.0, 0.0, 0.0), gamma: float = 1e-4, device="cuda", launcher=None, clock=None,
+                 allocator=None, stream_factory=None):
+        self.trees = trees
+        resident = sum(int(t.info()["bytes"]) for t in trees) if launcher is None else 0
+        self.adm = Admission(hbm_budget_bytes, resident)
+        self.n_streams = streams
+        self.max_rays = max_rays_per_launch
+        self.bg, self.gamma, self.device = tuple(bg), float(gamma), device
+        self.clock = clock or time.perf_counter
+        # injectable for host-only tests
+        self.launcher = launcher or self._launch_gpu
+        self.allocator = allocator or self._alloc_gpu
+        self.stream_factory = stream_factory or self._streams_gpu
+
+    # -- GPU plumbing -------------------------------------------------------
+    def _alloc_gpu(self, req: Request):
+        import torch
+        return torch.empty((int(req.cam["height"]), int(req.cam["width"]), 3), dtype=torch.float32,
+                           device=self.device)
+
+    def _streams_gpu(self, n):
+        import torch
+        return [torch.cuda.Stream(device=self.device) for _ in range(n)]
+
+    def _launch_gpu(self, reqs, stream):
+        import torch
+        items = [(self.trees[r.tree_id], r.cam, r.rgb, self.bg, self.gamma, None) for r in reqs]
+        with torch.cuda.stream(stream):
+            render_batch(items, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return ev
+
+    # -- the loop -------------------------------------------------------------
+    def run(self, requests, mode: str = "batch"):
+        """Serves ``requests`` (sorted by arrival) in real time; returns the requests with timestamps."""
+        assert mode in ("batch", "alone")
+        n_streams = self.n_streams if mode == "batch" else 1
+        per_launch = None if mode == "batch" else 1
+        streams = self.stream_factory(n_streams)
+        free = collections.deque(range(n_streams))
+        arrivals = collections.deque(requests)
+        waiting = collections.deque()
+        ready = collections.deque()
+        inflight = []               # (stream index, event, [requests])
+        t0 = self.clock()
+        now = 0.0
+        while arrivals or waiting or ready or inflight:
+            now = self.clock() - t0
+            while arrivals and arrivals[0].arrival <= now:
+                waiting.append(arrivals.popleft())
+            # admission in arrival order, by HBM footprint of the output; a
+            # request that cannot fit even into an idle server is rejected
+            while waiting:
+                r = waiting[0]
+                r.out_bytes = 12 * r.rays
+                if self.adm.resident + r.out_bytes > self.adm.budget:
+                    waiting.popleft()
+                    r.rejected = True
+                    r.t_done = now
+                    continue
+                if not self.adm.take(r.out_bytes):
+                    break
+                waiting.popleft()
+                r.rgb = self.allocator(r)
+                r.t_admit = now
+                ready.append(r)
+            # completions
+            still = []
+            for si, ev, reqs in inflight:
+                if ev.query():
+                    t = self.clock() - t0
+                    for r in reqs:
+                        r.t_done = t
+                        self.adm.release(r.out_bytes)
+                    free.append(si)
+                else:
+                    still.append((si, ev, reqs))
+            inflight = still
+            # launches: everything admitted so far (up to the ray cap) in one work list
+            while ready and free:
+                batch, rays = [], 0
+                while ready and (not batch or rays + ready[0].rays <= self.max_rays):
+                    if per_launch is not None and len(batch) >= per_launch:
+                        break
+                    r = ready.popleft()
+                    batch.append(r)
+                    rays += r.rays
+                si = free.popleft()
+                t = self.clock() - t0
+                for r in batch:
+                    r.t_launch = t
+                inflight.append((si, self.launcher(batch, streams[si]), batch))
+            if not (ready and free) and not (arrivals and arrivals[0].arrival <= self.clock() - t0):
+                time.sleep(2e-5)
+        return requests
+
+
+def summarize(requests, wall: float | None = None) -> dict:
+    rejected = sum(1 for r in requests if r.rejected)
+    requests = [r for r in requests if not r.rejected]
+    lat = np.array([r.t_done - r.arrival for r in requests]) * 1e3
+    rays = sum(r.rays for r in requests)
+    t_end = max(r.t_done for r in requests)
+    t_start = min(r.arrival for r in requests)
+    span = wall if wall is not None else (t_end - t_start)
+    return {"requests": len(requests), "rejected": rejected, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "max_ms": round(float(lat.max()), 3), "rays": int(rays),
+            "mrays_s": round(rays / span / 1e6, 2), "span_s": round(span, 4)}

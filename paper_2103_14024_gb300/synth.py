@@ -411,3 +411,138 @@ def random_rays(seed: int, n: int, radius: float = 4.0, spread: float = 0.6):
     tgt = np.stack([uniform(seed, 62 + a, ids) * 2.0 - 1.0 for a in range(3)], axis=1) * spread
     d = (tgt - o) * (0.5 + uniform(seed, 65, ids))[:, None]
     return o.astype(np.float32), d.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# The same generators evaluated with torch on a GPU (for trees with tens of
+# millions of leaves).  Integer hashing is bit-identical to the numpy path;
+# the float transforms (log, cos, exp) may differ in the last ulp.
+# ----------------------------------------------------------------------------
+
+def _t_consts(torch, device):
+    def s64(v):
+        return torch.tensor(v - (1 << 64) if v >= (1 << 63) else v, dtype=torch.int64, device=device)
+    return s64(0x9E3779B97F4A7C15), s64(0xBF58476D1CE4E5B9), s64(0x94D049BB133111EB)
+
+
+def _t_srl(x, k):
+    """Logical right shift of int64 tensors holding uint64 bit patterns."""
+    return (x >> k) & ((1 << (64 - k)) - 1)
+
+
+def _t_splitmix64(torch, x):
+    g, m1, m2 = _t_consts(torch, x.device)
+    z = x + g
+    z = (z ^ _t_srl(z, 30)) * m1
+    z = (z ^ _t_srl(z, 27)) * m2
+    return z ^ _t_srl(z, 31)
+
+
+def _t_hash(torch, seed, stream, codes):
+    key = int(_stream_key(seed, stream))
+    key = key - (1 << 64) if key >= (1 << 63) else key
+    return _t_splitmix64(torch, codes ^ key)
+
+
+def t_uniform(torch, seed, stream, codes):
+    h = _t_hash(torch, seed, stream, codes)
+    return _t_srl(h, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def t_normal_pair(torch, seed, stream, codes):
+    h = _t_hash(torch, seed, stream, codes)
+    u1 = (_t_srl(h, 32).to(torch.float64) + 0.5) * (1.0 / 4294967296.0)
+    u2 = (h & 0xFFFFFFFF).to(torch.float64) * (1.0 / 4294967296.0)
+    r = torch.sqrt(-2.0 * torch.log(u1))
+    a = 2.0 * math.pi * u2
+    return r * torch.cos(a), r * torch.sin(a)
+
+
+def _t_morton(torch, x, y, z, depth):
+    m = torch.zeros_like(x)
+    for b in range(depth):
+        m |= ((x >> b) & 1) << (3 * b + 2)
+        m |= ((y >> b) & 1) << (3 * b + 1)
+        m |= ((z >> b) & 1) << (3 * b)
+    return m
+
+
+def scene_shapes_torch(seed: int = 1001, depth: int = 9, sh_degree: int = 3, occupancy: float = 0.03,
+                       device="cuda", name: str = "main") -> Scene:
+    """``scene_shapes`` evaluated on a GPU; morton / sigma / sh are torch tensors
+    (morton as int64 bit patterns) on ``device``."""
+    import torch
+    lo, size = (-1.5, -1.5, -1.5), 3.0
+    centers, radius, half = _shapes(seed)
+    coarse = min(depth, 7)
+    target = occupancy * (1 << (3 * coarse))
+    s_lo, s_hi = 0.2, 4.0
+    for _ in range(40):
+        s_mid = 0.5 * (s_lo + s_hi)
+        n = _occupied_codes(coarse, lo, size, centers, radius, half, s_mid).shape[0]
+        if n < target:
+            s_lo = s_mid
+        else:
+            s_hi = s_mid
+    scale = 0.5 * (s_lo + s_hi)
+    R = 1 << depth
+    h = size / R
+    codes = []
+    for i in range(centers.shape[0]):
+        c = centers[i]
+        ext = (radius[i] if i % 2 == 0 else half[i].max()) * scale
+        lo_i = np.clip(np.floor((c - ext - lo[0]) / h - 0.5).astype(int), 0, R - 1)
+        hi_i = np.clip(np.ceil((c + ext - lo[0]) / h + 0.5).astype(int), 0, R - 1)
+        ax = [torch.arange(int(lo_i[a]), int(hi_i[a]) + 1, device=device, dtype=torch.int64) for a in range(3)]
+        for xs in torch.split(ax[0], 64):
+            X, Y, Z = torch.meshgrid(xs, ax[1], ax[2], indexing="ij")
+            px = lo[0] + (X.to(torch.float64) + 0.5) * h
+            py = lo[1] + (Y.to(torch.float64) + 0.5) * h
+            pz = lo[2] + (Z.to(torch.float64) + 0.5) * h
+            if i % 2 == 0:
+                m = (px - c[0]) ** 2 + (py - c[1]) ** 2 + (pz - c[2]) ** 2 < (radius[i] * scale) ** 2
+            else:
+                hs = half[i] * scale
+                m = ((px - c[0]).abs() < hs[0]) & ((py - c[1]).abs() < hs[1]) & ((pz - c[2]).abs() < hs[2])
+            codes.append(_t_morton(torch, X[m], Y[m], Z[m], depth))
+    codes = torch.unique(torch.cat(codes)) if codes else torch.zeros(0, dtype=torch.int64, device=device)
+    z0, _ = t_normal_pair(torch, seed, 30, codes)
+    sigma = torch.exp(3.0 + z0).to(torch.float32)
+    K = (sh_degree + 1) ** 2
+    sh = torch.empty((codes.shape[0], K, 3), dtype=torch.float32, device=device)
+    flat = [(k, c) for k in range(K) for c in range(3)]
+    for p in range(0, len(flat), 2):
+        z0, z1 = t_normal_pair(torch, seed, 1000 + p // 2, codes)
+        for zz, idx in ((z0, p), (z1, p + 1)):
+            if idx < len(flat):
+                k, c = flat[idx]
+                sh[:, k, c] = (zz * (0.5 / (int(math.isqrt(k)) + 1))).to(torch.float32)
+    return Scene(depth, lo, size, sh_degree, codes, sigma, sh, name=name)
+
+
+# ----------------------------------------------------------------------------
+# Serving workload: Poisson arrivals of render requests on resident trees
+# ----------------------------------------------------------------------------
+
+SERVE_TREES = ((7, 1), (8, 2), (9, 3), (10, 3))            # (depth, SH degree), fp16 leaves
+SERVE_RESOLUTIONS = ((256, 256), (512, 512), (800, 800), (1920, 1080))
+
+
+def serve_requests(seed: int, n: int, rate_hz: float = 300.0, n_trees: int = 4):
+    """n requests: arrival times (s) of a Poisson process of ``rate_hz``, a tree
+    index, and one camera each (random orbit position at radius 4, elevation
+    10..50 degrees, looking at the origin; focal 1111 px scaled with width)."""
+    ids = np.arange(n, dtype=np.uint64)
+    gaps = -np.log(1.0 - uniform(seed, 70, ids)) / rate_hz
+    arrival = np.cumsum(gaps) - gaps[0]
+    tree = (uniform(seed, 71, ids) * n_trees).astype(np.int64)
+    res = (uniform(seed, 72, ids) * len(SERVE_RESOLUTIONS)).astype(np.int64)
+    az = uniform(seed, 73, ids) * 2.0 * math.pi
+    el = np.radians(10.0 + 40.0 * uniform(seed, 74, ids))
+    cams = []
+    for i in range(n):
+        W, H = SERVE_RESOLUTIONS[res[i]]
+        eye = (4.0 * math.cos(el[i]) * math.cos(az[i]), 4.0 * math.cos(el[i]) * math.sin(az[i]),
+               4.0 * math.sin(el[i]))
+        cams.append(make_cameras([look_at(eye)], W, H, 1111.0 * W / 800.0, near=2.0, far=6.0)[0])
+    return arrival, tree, cams
