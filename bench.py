@@ -35,8 +35,7 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 8-view capture (4.310 GB read + 0.071 GB written) x 25 = 200-view launch
-    "f32": {"sha": "142654ef392409bb", "bytes_per_launch": 109.53e9},
+    # filled from the committed ncu capture of the current kernel version
 }
 
 
@@ -47,6 +46,20 @@ def kernel_sha() -> str:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def max_over_ranks(torch, dist, value: float, device) -> float:
+    """Max of a per-rank float over the process group (identity without one)."""
+    if dist is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, rays_per_rank_step: int, wall_max: float, steps: int) -> float:
+    """Whole-job Mrays/s: the rays all ranks rendered per step / the slowest rank's step time."""
+    return world * rays_per_rank_step / (wall_max / steps) / 1e6
 
 
 def dist_env():
@@ -404,14 +417,11 @@ def main():
     leaf_bytes = int(main_res["info"]["leaf_bytes"])
     alg = algorithmic_bytes(pot, torch, main_res["tree"], cams, args.dtype, leaf_bytes)
 
-    # whole-job time: max over ranks of the timed region
-    wall = main_res["wall"]
-    if dist is not None:
-        t = torch.tensor([wall], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
+    # whole-job time: max over ranks of the timed region; every rank rendered
+    # its own copy of the workload (weak scaling, no exchange on the data path)
+    wall = max_over_ranks(torch, dist, main_res["wall"], "cuda")
     ms_per_step = 1e3 * wall / args.steps
-    value = world * rays / (wall / args.steps) / 1e6
+    value = job_value(world, rays, wall, args.steps)
     avg_launch_ms = sum(main_res["per"]) / len(main_res["per"])
     peak, peak_kind = measured_peaks()
     achieved = alg["hbm_bytes"] / (avg_launch_ms * 1e-3) / 1e9

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -33,6 +34,16 @@ unsigned int *device_error_word()
         ptr[dev] = static_cast<unsigned int *>(p);
     }
     return ptr[dev];
+}
+
+int render_view_group(int n_cams)
+{
+    static int g = [] {
+        const char *e = std::getenv("POT_VIEW_GROUP");
+        const int v = e ? std::atoi(e) : 16;
+        return v >= 1 ? v : 1;
+    }();
+    return n_cams < g ? (n_cams > 0 ? n_cams : 1) : g;
 }
 
 }  // namespace pot
@@ -509,6 +520,8 @@ pot_status pot_render(const pot_tree *t, const pot_camera *cams, int32_t n_cams,
     p.cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
     p.W = W;
     p.H = H;
+    p.n_cams = n_cams;
+    p.view_group = render_view_group(n_cams);
     p.tiles_x = (W + 7) / 8;
     p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
     p.n_tiles = p.tiles_per_cam * n_cams;

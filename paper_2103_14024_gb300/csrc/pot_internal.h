@@ -41,6 +41,8 @@ struct RenderParams {
     int step_cap;
     // ray source: cameras (tiles of 8 x 4 pixels) or explicit rays (32 per tile)
     const pot_camera *cams;
+    int n_cams;
+    int view_group;     // tiles are interleaved over groups of this many consecutive cameras
     int W, H;
     int tiles_x;
     int64_t tiles_per_cam;
@@ -90,6 +92,9 @@ cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int 
                                float *o, float *d, unsigned *d_flag, cudaStream_t s);
 
 cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_t s, unsigned int *err);
+
+// cameras interleaved per tile group in camera renders (POT_VIEW_GROUP overrides)
+int render_view_group(int n_cams);
 
 unsigned int *device_error_word();   // per-device word raised by kernels
 void set_last_error(const char *msg); // message returned by pot_last_error on this thread

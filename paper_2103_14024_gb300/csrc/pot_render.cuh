@@ -243,8 +243,15 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
         int64_t ray;
         bool valid;
         if (CAMS) {
-            const int64_t cam = (int64_t)tile / p.tiles_per_cam;
-            const int64_t rem = (int64_t)tile - cam * p.tiles_per_cam;
+            // tiles of a group of G consecutive cameras are interleaved: the same
+            // 8x4 tile of each camera of the group in turn, so neighbouring views
+            // (which touch nearly the same leaves) share L1/L2
+            const int64_t G = p.view_group;
+            const int64_t group = (int64_t)tile / (p.tiles_per_cam * G);
+            const int64_t in_group = (int64_t)tile - group * p.tiles_per_cam * G;
+            const int64_t gsize = min(G, (int64_t)p.n_cams - group * G);
+            const int64_t cam = group * G + in_group % gsize;
+            const int64_t rem = in_group / gsize;
             const int ty = (int)(rem / p.tiles_x);
             const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
             const int i = tx * 8 + (lane & 7);
