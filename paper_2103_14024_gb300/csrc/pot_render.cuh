@@ -26,81 +26,35 @@ constexpr int kBlock = 256;
 #define POT_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
 #endif
 
-// Walks one ray through the octree (a2-a4) and calls vis(leaf, delta, Y) for
-// every leaf segment of positive length in order (Y: the SH basis at the ray
-// direction); the walk ends when vis returns true, at the far clip, or when
-// the ray leaves the box.  The next cell is located and its leaf prefetched
-// before vis runs on the current one.
-template <int K, typename T, typename Visitor>
-__device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
-                                         int32_t *stk, const float o[3], const float d[3], float near,
-                                         float far, Visitor &vis)
-{
-    const int D = p.depth;
-    const int R = p.R;
-    const float h = p.h, invh = p.invh;
-    const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-    if (!(len > 0.f) || !(len < 3.0e38f)) return;
-    const float invlen = __frcp_rn(len);
-
+// One ray's walk through the octree (a2-a4) as resumable state: begin() sets
+// the ray up (clip, locate, first descent), step() advances one cell and calls
+// vis(leaf, delta, Y) for a leaf segment of positive length (Y: the SH basis at
+// the ray direction), returning false once the walk is over (vis returned
+// true, far clip, or the ray left the box).  The next cell is located and its
+// leaf prefetched before vis runs on the current one.
+template <int K, typename T>
+struct Walker {
+    float d[3], rd[3], Ahi[3], Alo[3], margin[3];
+    float len;
     float Y[K];
-    sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y);
-
-    float Ahi[3], Alo[3], rd[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
-        rd[a] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
-    }
-
-    // a2: clip range in units of the ray parameter t (position o + t d)
-    df tin = {near * invlen, 0.f};
-    df tout = {far * invlen, 0.f};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (d[a] == 0.f) {
-            float s, e;
-            two_sum(o[a], -p.lo[a], s, e);
-            const bool inside = (s > 0.f || (s == 0.f && e >= 0.f)) && (s < p.size || (s == p.size && e < 0.f));
-            if (!inside) return;
-        } else {
-            df t0 = cross_time(0, h, Ahi[a], Alo[a], d[a], rd[a]);
-            df t1 = cross_time(R, h, Ahi[a], Alo[a], d[a], rd[a]);
-            if (d[a] < 0.f) {
-                df tmp = t0;
-                t0 = t1;
-                t1 = tmp;
-            }
-            if (df_lt(tin, t0)) tin = t0;
-            if (df_lt(t1, tout)) tout = t1;
-        }
-    }
-    if (!df_lt(tin, tout)) return;
-
-    // error bound of the fp32 voxel-coordinate estimate, in voxels
-    float margin[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        margin[a] = (fabsf(tout.hi * d[a]) + fabsf(Ahi[a])) * invh * 3.8146973e-6f + 1e-6f;
-
+    df t, tout;
     int q[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int v = locate_axis(tin, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
-        q[a] = min(max(v, 0), R - 1);
-    }
+    int leaf, cell_lvl, lvl_valid, step_i;
+    int kx[3];
+    df tcx[3];
 
     // a3: descend to the cell of voxel nq from the deepest ancestor it shares
     // with voxel pq (whose path the stack holds up to lvl_valid)
-    int lvl_valid = 0;
-    stk[0] = 0;
-    auto descend = [&](const int nq[3], const int pq[3], int &leaf, int &cell_lvl) {
+    __device__ __forceinline__ void descend(const RenderParams &p, int32_t *stk, const int nq[3], const int pq[3],
+                                            int &out_leaf, int &out_lvl)
+    {
+        const int D = p.depth;
         const unsigned diff = (unsigned)((nq[0] ^ pq[0]) | (nq[1] ^ pq[1]) | (nq[2] ^ pq[2]));
         const int lc = diff ? D - 32 + __clz(diff) : D - 1;  // level of the common ancestor
         int l = min(lc, lvl_valid);
         int node = stk[l * kBlock];
-        leaf = -1;
-        cell_lvl = D;
+        out_leaf = -1;
+        out_lvl = D;
         for (; l < D; ++l) {
             const int b = D - 1 - l;
             const int s = (((nq[0] >> b) & 1) << 2) | (((nq[1] >> b) & 1) << 1) | ((nq[2] >> b) & 1);
@@ -110,23 +64,81 @@ __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr
                 stk[(l + 1) * kBlock] = c;
                 continue;
             }
-            if (c < 0) leaf = -c - 1;
-            else cell_lvl = l + 1;
+            if (c < 0) out_leaf = -c - 1;
+            else out_lvl = l + 1;
             break;
         }
         lvl_valid = min(l, D - 1);
-    };
+    }
 
-    int leaf, cell_lvl;
-    descend(q, q, leaf, cell_lvl);
-    if (leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
+    __device__ __forceinline__ bool begin(const RenderParams &p, int32_t *stk, const T *sig_arr, const T *sh_arr,
+                                          const float o[3], const float dir[3], float near, float far)
+    {
+        const int R = p.R;
+        const float h = p.h, invh = p.invh;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = dir[a];
+        len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+        if (!(len > 0.f) || !(len < 3.0e38f)) return false;
+        const float invlen = __frcp_rn(len);
+        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
+            rd[a] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
+        }
+        // a2: clip range in units of the ray parameter t (position o + t d)
+        df tin = {near * invlen, 0.f};
+        tout = {far * invlen, 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (d[a] == 0.f) {
+                float s, e;
+                two_sum(o[a], -p.lo[a], s, e);
+                const bool inside = (s > 0.f || (s == 0.f && e >= 0.f)) && (s < p.size || (s == p.size && e < 0.f));
+                if (!inside) return false;
+            } else {
+                df t0 = cross_time(0, h, Ahi[a], Alo[a], d[a], rd[a]);
+                df t1 = cross_time(R, h, Ahi[a], Alo[a], d[a], rd[a]);
+                if (d[a] < 0.f) {
+                    df tmp = t0;
+                    t0 = t1;
+                    t1 = tmp;
+                }
+                if (df_lt(tin, t0)) tin = t0;
+                if (df_lt(t1, tout)) tout = t1;
+            }
+        }
+        if (!df_lt(tin, tout)) return false;
+        // error bound of the fp32 voxel-coordinate estimate, in voxels
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            margin[a] = (fabsf(tout.hi * d[a]) + fabsf(Ahi[a])) * invh * 3.8146973e-6f + 1e-6f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int v = locate_axis(tin, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+            q[a] = min(max(v, 0), R - 1);
+        }
+        lvl_valid = 0;
+        stk[0] = 0;
+        descend(p, stk, q, q, leaf, cell_lvl);
+        if (leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
+        // exit plane (voxel index) and crossing time per axis, recomputed only
+        // when the plane changes (once per step inside runs of leaves)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) kx[a] = -0x40000000;
+        t = tin;
+        step_i = 0;
+        return true;
+    }
 
-    // exit plane (voxel index) and crossing time per axis, recomputed only
-    // when the plane changes (once per step inside runs of leaves)
-    int kx[3] = {-0x40000000, -0x40000000, -0x40000000};
-    df tcx[3];
-    df t = tin;
-    for (int step = 0;; ++step) {
+    template <typename Visitor>
+    __device__ __forceinline__ bool step(const RenderParams &p, int32_t *stk, const T *sig_arr, const T *sh_arr,
+                                         Visitor &vis)
+    {
+        const int D = p.depth;
+        const int R = p.R;
+        const float h = p.h, invh = p.invh;
         // a4: exit of the current cell
         const int sz = 1 << (D - cell_lvl);
         int qb[3];
@@ -159,7 +171,7 @@ __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr
         int nq[3] = {q[0], q[1], q[2]};
         int nleaf = -1, nlvl = D;
         if (!last) {
-            if (step >= p.step_cap) {
+            if (step_i >= p.step_cap) {
                 atomicOr(p.err, 1u);
                 stop = true;
             } else {
@@ -178,21 +190,34 @@ __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr
                 if (outside) {
                     stop = true;
                 } else {
-                    descend(nq, q, nleaf, nlvl);
+                    descend(p, stk, nq, q, nleaf, nlvl);
                     if (nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
                 }
             }
         }
-
         if (leaf >= 0 && dt > 0.f) {
-            if (vis(leaf, dt * len, Y)) break;
+            if (vis(leaf, dt * len, Y)) return false;
         }
-        if (stop) break;
+        if (stop) return false;
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[a] = nq[a];
         leaf = nleaf;
         cell_lvl = nlvl;
         if (df_lt(t, texit)) t = texit;
+        ++step_i;
+        return true;
+    }
+};
+
+// The whole walk of one ray.
+template <int K, typename T, typename Visitor>
+__device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
+                                         int32_t *stk, const float o[3], const float d[3], float near,
+                                         float far, Visitor &vis)
+{
+    Walker<K, T> w;
+    if (!w.begin(p, stk, sig_arr, sh_arr, o, d, near, far)) return;
+    while (w.step(p, stk, sig_arr, sh_arr, vis)) {
     }
 }
 
@@ -224,6 +249,66 @@ struct ShadeVisitor {
     }
 };
 
+// Ray (origin, direction, clip range, output index) of slot `slot` (0..31) of
+// tile `tile`: 8x4 pixels of a camera (tiles interleaved over groups of
+// adjacent cameras) or 32 consecutive explicit rays.  False for slots outside
+// the image or past the last ray.
+template <bool CAMS>
+__device__ __forceinline__ bool tile_ray(const RenderParams &p, unsigned long long tile, int slot, float o[3],
+                                         float d[3], float &near, float &far, int64_t &ray)
+{
+    if (CAMS) {
+        // tiles of a group of G consecutive cameras are interleaved: the same
+        // 8x4 tile of each camera of the group in turn, so neighbouring views
+        // (which touch nearly the same leaves) share L1/L2
+        const int64_t G = p.view_group;
+        const int64_t group = (int64_t)tile / (p.tiles_per_cam * G);
+        const int64_t in_group = (int64_t)tile - group * p.tiles_per_cam * G;
+        const int64_t gsize = min(G, (int64_t)p.n_cams - group * G);
+        const int64_t cam = group * G + in_group % gsize;
+        const int64_t rem = in_group / gsize;
+        const int ty = (int)(rem / p.tiles_x);
+        const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
+        const int i = tx * 8 + (slot & 7);
+        const int j = ty * 4 + (slot >> 3);
+        if (i >= p.W || j >= p.H) return false;
+        ray = (cam * p.H + j) * p.W + i;
+        const pot_camera *c = p.cams + cam;
+        // a1: pixel ray, each operation rounded once in the stated order
+        const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), c->cx), c->fx);
+        const float yc = -__fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), c->cy), c->fy);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            d[r] = __fsub_rn(__fadd_rn(__fmul_rn(c->c2w[r][0], xc), __fmul_rn(c->c2w[r][1], yc)), c->c2w[r][2]);
+            o[r] = c->c2w[r][3];
+        }
+        near = c->near;
+        far = c->far;
+        return true;
+    }
+    ray = (int64_t)tile * 32 + slot;
+    if (ray >= p.n_rays) return false;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        o[r] = __ldg(p.ray_o + 3 * ray + r);
+        d[r] = __ldg(p.ray_d + 3 * ray + r);
+    }
+    near = p.near;
+    far = p.far;
+    return true;
+}
+
+template <int K, typename T, bool COUNT>
+__device__ __forceinline__ void store_ray(const RenderParams &p, int64_t ray, const ShadeVisitor<K, T, COUNT> &v)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p.rgb[3 * ray + c] = fmaf(v.Tr, p.bg[c], v.col[c]);
+    if (p.t_final) p.t_final[ray] = v.Tr;
+    if (COUNT) p.seg_count[ray] = v.nseg;
+}
+
+// Forward render, one tile per warp at a time: the warp takes the next tile
+// once all 32 of its rays are done.
 template <int K, typename T, bool CAMS, bool COUNT>
 __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(const RenderParams p)
 {
@@ -232,64 +317,17 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
     const int lane = threadIdx.x & 31;
     const T *sig_arr = static_cast<const T *>(p.sigma);
     const T *sh_arr = static_cast<const T *>(p.sh);
-
     for (;;) {
         unsigned long long tile = 0;
         if (lane == 0) tile = atomicAdd(p.tile_counter, 1ull);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= (unsigned long long)p.n_tiles) break;
-
         float o[3], d[3], near, far;
         int64_t ray;
-        bool valid;
-        if (CAMS) {
-            // tiles of a group of G consecutive cameras are interleaved: the same
-            // 8x4 tile of each camera of the group in turn, so neighbouring views
-            // (which touch nearly the same leaves) share L1/L2
-            const int64_t G = p.view_group;
-            const int64_t group = (int64_t)tile / (p.tiles_per_cam * G);
-            const int64_t in_group = (int64_t)tile - group * p.tiles_per_cam * G;
-            const int64_t gsize = min(G, (int64_t)p.n_cams - group * G);
-            const int64_t cam = group * G + in_group % gsize;
-            const int64_t rem = in_group / gsize;
-            const int ty = (int)(rem / p.tiles_x);
-            const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
-            const int i = tx * 8 + (lane & 7);
-            const int j = ty * 4 + (lane >> 3);
-            valid = i < p.W && j < p.H;
-            ray = (cam * p.H + j) * p.W + i;
-            const pot_camera *c = p.cams + cam;
-            // a1: pixel ray, each operation rounded once in the stated order
-            const float xc = __fdiv_rn(__fsub_rn(__fadd_rn((float)i, 0.5f), c->cx), c->fx);
-            const float yc = -__fdiv_rn(__fsub_rn(__fadd_rn((float)j, 0.5f), c->cy), c->fy);
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                d[r] = __fsub_rn(__fadd_rn(__fmul_rn(c->c2w[r][0], xc), __fmul_rn(c->c2w[r][1], yc)),
-                                 c->c2w[r][2]);
-                o[r] = c->c2w[r][3];
-            }
-            near = c->near;
-            far = c->far;
-        } else {
-            ray = (int64_t)tile * 32 + lane;
-            valid = ray < p.n_rays;
-            if (valid) {
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    o[r] = __ldg(p.ray_o + 3 * ray + r);
-                    d[r] = __ldg(p.ray_d + 3 * ray + r);
-                }
-            }
-            near = p.near;
-            far = p.far;
-        }
-        if (valid) {
+        if (tile_ray<CAMS>(p, tile, lane, o, d, near, far, ray)) {
             ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
             walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, near, far, v);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) p.rgb[3 * ray + c] = fmaf(v.Tr, p.bg[c], v.col[c]);
-            if (p.t_final) p.t_final[ray] = v.Tr;
-            if (COUNT) p.seg_count[ray] = v.nseg;
+            store_ray<K, T, COUNT>(p, ray, v);
         }
     }
 }
