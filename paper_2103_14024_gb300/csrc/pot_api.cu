@@ -1,6 +1,7 @@
 // pot_api.cu -- the C ABI of libpot.so: argument checks, host/device staging,
 // error reporting, tree lifetime, and the launches.  Every numeric step runs in
 // the kernels of pot_build.cu, pot_query.cu and pot_render_*.cu.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -287,6 +288,87 @@ cudaError_t launch_render(const RenderParams &p, const pot_tree *t, bool cams, c
     }
 }
 
+// Per-device stream for device->host copies that overlap rendering.
+cudaError_t copy_stream(cudaStream_t *out)
+{
+    static std::mutex mu;
+    static cudaStream_t st[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev]) {
+        e = cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *out = st[dev];
+    return cudaSuccess;
+}
+
+// Camera render into host memory: the cameras are rendered in chunks (one view
+// group each) into two device staging buffers; the copy of chunk c to the host
+// runs on a second stream while chunk c + 1 renders.  Returns after the last
+// copy has completed.  p.tile_counter points at one zeroed counter per chunk.
+pot_status render_to_host(RenderParams p, const pot_tree *t, const pot_camera *d_cams, int n_cams, float *rgb,
+                          float *t_final, cudaStream_t s)
+{
+    const int64_t per_cam = (int64_t)p.W * p.H;
+    const int chunk = render_view_group(n_cams);
+    const int n_chunks = (n_cams + chunk - 1) / chunk;
+    const bool rgb_dev = is_device_ptr(rgb);
+    const bool tf_dev = t_final && is_device_ptr(t_final);
+    cudaStream_t cs;
+    POT_CUDA(copy_stream(&cs), "copy stream");
+    Tmp stage[2], stage_tf[2];
+    cudaEvent_t rendered[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    struct Events {
+        cudaEvent_t *a, *b;
+        ~Events()
+        {
+            for (int i = 0; i < 2; ++i) {
+                if (a[i]) cudaEventDestroy(a[i]);
+                if (b[i]) cudaEventDestroy(b[i]);
+            }
+        }
+    } guard{rendered, copied};
+    for (int i = 0; i < 2; ++i) {
+        POT_CUDA(cudaEventCreateWithFlags(&rendered[i], cudaEventDisableTiming), "event");
+        POT_CUDA(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming), "event");
+        if (!rgb_dev) POT_CUDA(stage[i].alloc(sizeof(float) * 3 * per_cam * chunk, s), "alloc stage");
+        if (t_final && !tf_dev) POT_CUDA(stage_tf[i].alloc(sizeof(float) * per_cam * chunk, s), "alloc stage");
+    }
+    for (int c = 0; c < n_chunks; ++c) {
+        const int b = c & 1;
+        const int c0 = c * chunk, nc = std::min(chunk, n_cams - c0);
+        if (c >= 2) POT_CUDA(cudaStreamWaitEvent(s, copied[b], 0), "wait copy");
+        RenderParams q = p;
+        q.cams = d_cams + c0;
+        q.n_cams = nc;
+        q.view_group = nc;
+        q.n_tiles = p.tiles_per_cam * nc;
+        q.rgb = rgb_dev ? rgb + 3 * per_cam * c0 : static_cast<float *>(stage[b].p);
+        q.t_final = !t_final ? nullptr : (tf_dev ? t_final + per_cam * c0 : static_cast<float *>(stage_tf[b].p));
+        q.tile_counter = p.tile_counter + c;
+        POT_CUDA(launch_render(q, t, true, s), "render");
+        POT_CUDA(cudaEventRecord(rendered[b], s), "record");
+        POT_CUDA(cudaStreamWaitEvent(cs, rendered[b], 0), "wait render");
+        if (!rgb_dev)
+            POT_CUDA(cudaMemcpyAsync(rgb + 3 * per_cam * c0, stage[b].p, sizeof(float) * 3 * per_cam * nc,
+                                     cudaMemcpyDeviceToHost, cs),
+                     "copy rgb");
+        if (t_final && !tf_dev)
+            POT_CUDA(cudaMemcpyAsync(t_final + per_cam * c0, stage_tf[b].p, sizeof(float) * per_cam * nc,
+                                     cudaMemcpyDeviceToHost, cs),
+                     "copy t_final");
+        POT_CUDA(cudaEventRecord(copied[b], cs), "record");
+    }
+    // the staging buffers are released on s: make s wait for the last copies
+    for (int b = 0; b < 2 && b < n_chunks; ++b) POT_CUDA(cudaStreamWaitEvent(s, copied[b], 0), "wait copy");
+    POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
 }  // namespace
 
 void pot::set_last_error(const char *msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
@@ -504,34 +586,32 @@ pot_status pot_render(const pot_tree *t, const pot_camera *cams, int32_t n_cams,
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t npix = (int64_t)n_cams * W * H;
     Tmp scratch;
-    const size_t cam_off = 256;
+    // tile counters (one per launch: a host-memory output renders in chunks), then the cameras
+    const size_t cam_off = ((sizeof(unsigned long long) * (size_t)(n_cams + 1) + 255) / 256) * 256;
     POT_CUDA(scratch.alloc(cam_off + sizeof(pot_camera) * n_cams, s), "alloc scratch");
     char *sp = static_cast<char *>(scratch.p);
-    POT_CUDA(cudaMemsetAsync(sp, 0, sizeof(unsigned long long), s), "memset");
+    POT_CUDA(cudaMemsetAsync(sp, 0, cam_off, s), "memset");
     POT_CUDA(cudaMemcpyAsync(sp + cam_off, cams, sizeof(pot_camera) * n_cams, cudaMemcpyHostToDevice, s),
              "copy cams");
-    Out orgb, otf;
-    void *drgb, *dtf = nullptr;
-    POT_CUDA(orgb.bind(rgb, sizeof(float) * 3 * npix, s, &drgb), "bind rgb");
-    if (t_final) POT_CUDA(otf.bind(t_final, sizeof(float) * npix, s, &dtf), "bind t_final");
     RenderParams p;
     fill_tree_params(p, t, opts);
     if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
-    p.cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
     p.W = W;
     p.H = H;
-    p.n_cams = n_cams;
-    p.view_group = render_view_group(n_cams);
     p.tiles_x = (W + 7) / 8;
     p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
-    p.n_tiles = p.tiles_per_cam * n_cams;
-    p.rgb = (float *)drgb;
-    p.t_final = (float *)dtf;
     p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
+    const pot_camera *d_cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
+    const bool host_out = !is_device_ptr(rgb) || (t_final && !is_device_ptr(t_final));
+    if (host_out) return render_to_host(p, t, d_cams, n_cams, rgb, t_final, s);
+    p.cams = d_cams;
+    p.n_cams = n_cams;
+    p.view_group = render_view_group(n_cams);
+    p.n_tiles = p.tiles_per_cam * n_cams;
+    p.rgb = rgb;
+    p.t_final = t_final;
     POT_CUDA(launch_render(p, t, true, s), "render");
-    POT_CUDA(orgb.finish(s), "copy rgb");
-    POT_CUDA(otf.finish(s), "copy t_final");
-    if (orgb.host || otf.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    (void)npix;
     return POT_OK;
 }
 

@@ -234,6 +234,26 @@ def test_render_host_buffers(pot, oracle_mod):
     assert np.abs(host.numpy() - oracle_mod.render_cams(ot, cams)["rgb"]).max() <= TOL
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_render_host_output_chunked(pot, torch_mod, pinned):
+    """Host outputs are rendered in view groups and copied back while the next
+    group renders; the images equal a device-output render bit for bit."""
+    torch = torch_mod
+    sc = S.scene_random(47, 5, 2, p_occ=0.35)
+    t = pot.Tree.from_scene(sc)
+    cams = S.make_cameras(S.orbit_c2ws(41, radius=3.0), 33, 21, 30.0)      # 3 groups of 16 + ragged tile
+    ref, ref_tf = pot.render(t, cams, gamma=1e-4, want_t_final=True)
+    host = torch.full((41, 21, 33, 3), -1.0, pin_memory=pinned)
+    host_tf = torch.full((41, 21, 33), -1.0, pin_memory=pinned)
+    pot.render(t, cams, rgb=host, t_final=host_tf, gamma=1e-4)
+    assert torch.equal(host, ref.cpu()) and torch.equal(host_tf, ref_tf.cpu())
+    # host rgb with a device t_final
+    dev_tf = torch.full((41, 21, 33), -1.0, device="cuda")
+    host2 = torch.full((41, 21, 33, 3), -1.0)
+    pot.render(t, cams, rgb=host2, t_final=dev_tf, gamma=1e-4)
+    assert torch.equal(host2, ref.cpu()) and torch.equal(dev_tf, ref_tf)
+
+
 def test_render_edge_cases(pot, oracle_mod, torch_mod):
     sc = S.scene_random(44, 4, 2, p_occ=0.4, sigma_mu=1.0)
     sig = sc.sigma.copy()
