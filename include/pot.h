@@ -259,6 +259,23 @@ pot_status pot_camera_rays(const pot_camera *cams, int32_t n_cams, int64_t n, co
 pot_status pot_render_noalloc(const pot_tree *tree, const pot_camera *cams, int32_t n_cams,
                               const pot_render_opts *opts, float *rgb, float *t_final, pot_stream stream);
 
+/* ------------------------------------------------------------ filtering ---
+ * Sec. 3.2 "Filtering": render the cameras and keep, for every leaf, the
+ * largest ray weight w_i = T_i (1 - exp(-max(sigma_i,0) delta_i)) it receives
+ * (compositing and early stop as in pot_render; bg unused).  Updates
+ * max_weight [n_leaves] (device memory, float32) to max(old, new): the caller
+ * initialises it (zeros) and may accumulate over several calls.  cams: host
+ * memory, same width and height.                                           */
+pot_status pot_visibility(const pot_tree *tree, const pot_camera *cams, int32_t n_cams,
+                          const pot_render_opts *opts, float *max_weight, pot_stream stream);
+
+/* A new tree holding the leaves of `tree` whose score >= threshold (score
+ * [n_leaves] in device memory, e.g. pot_visibility's max_weight), with the
+ * same depth, box, SH degree, dtype and leaf values; the tree is empty
+ * elsewhere, so empty space grows where leaves were dropped.  Synchronises. */
+pot_status pot_tree_prune(const pot_tree *tree, const float *score, float threshold, pot_tree **out,
+                          pot_stream stream);
+
 /* ---------------------------------------------------------------- batch ---
  * Many render requests in one call -- the work list of a continuous-batching
  * server (the paper's real-time viewer renders one view at a time, Sec. 4.5;

@@ -77,6 +77,7 @@ def _declare(L):
     L.oracle_render_cams.argtypes = [_p, _p, C.c_int, _p, _dbl, _p, _p, _p, _p]
     L.oracle_render_pixels.argtypes = [_p, _p, _i64, _p, _p, _p, _p, _dbl, _p, _p, _p]
     L.oracle_backward_rays.argtypes = [_p, _i64, _p, _p, _dbl, _dbl, _p, _dbl, _p, _p, _p]
+    L.oracle_visibility.argtypes = [_p, _p, C.c_int, _dbl, _p]
 
 
 def _ptr(a):
@@ -264,6 +265,22 @@ def backward_rays(tree: OTree, o, d, grad_rgb, near=0.0, far=1e30, bg=(0.0, 0.0,
     lib().oracle_backward_rays(tree._h, o.shape[0], _ptr(o), _ptr(d), near, far, _ptr(bgv), gamma,
                                _ptr(g), _ptr(gs), _ptr(gh))
     return gs, gh
+
+
+def visibility(tree: OTree, cams, gamma=0.0):
+    """Largest ray weight T (1 - exp(-sigma delta)) each leaf receives over all
+    pixels of ``cams`` (Sec. 3.2 "Filtering"); float64 [n_leaves]."""
+    cams = np.ascontiguousarray(cams)
+    out = np.zeros(tree.n_leaves)
+    lib().oracle_visibility(tree._h, _ptr(cams), len(cams), gamma, _ptr(out))
+    return out
+
+
+def prune(scene, scores, threshold):
+    """The scene restricted to the voxels whose score >= threshold (the leaves of
+    the filtered octree, Sec. 3.2 "Filtering"), in their Morton order."""
+    keep = np.asarray(scores) >= threshold
+    return scene.replace(morton=scene.morton[keep], sigma=scene.sigma[keep], sh=scene.sh[keep])
 
 
 # ----------------------------------------------------------------------------

@@ -719,6 +719,52 @@ void oracle_render_pixels(const otree *t, const ocam *cams, int64_t n, const int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Visibility filtering (Sec. 3.2 "Filtering")                                */
+/* ------------------------------------------------------------------------ */
+
+/* For every leaf, the largest ray weight w_i = T_i (1 - exp(-sigma_i delta_i))
+ * it receives over all pixels of the cameras (compositing as in render_one,
+ * early stop included); 0 for leaves no ray composites.  max_w [n_leaves]. */
+void oracle_visibility(const otree *t, const ocam *cams, int n_cams, double gamma, double *max_w)
+{
+    int cap = seg_cap(t);
+    for (int64_t i = 0; i < t->n_leaves; ++i) max_w[i] = 0.0;
+    for (int c = 0; c < n_cams; ++c) {
+        const ocam *cam = &cams[c];
+        const int W = cam->width, H = cam->height;
+#pragma omp parallel
+        {
+            oseg *buf = (oseg *)malloc(sizeof(oseg) * (size_t)cap);
+#pragma omp for schedule(dynamic, 1)
+            for (int j = 0; j < H; ++j) {
+                for (int i = 0; i < W; ++i) {
+                    float o32[3], d32[3];
+                    cam_ray_f32(cam, i, j, o32, d32);
+                    double o[3] = {o32[0], o32[1], o32[2]}, d[3] = {d32[0], d32[1], d32[2]};
+                    int ns = trace(t, o, d, cam->near, cam->far, buf, cap);
+                    double T = 1.0;
+                    for (int k = 0; k < ns; ++k) {
+                        if (buf[k].leaf < 0) continue;
+                        double sig = t->sigma[buf[k].leaf];
+                        if (sig < 0) sig = 0;
+                        double x = sig * buf[k].delta;
+                        double w = T * (-expm1(-x));
+                        double *dst = max_w + buf[k].leaf;
+#pragma omp critical(visibility)
+                        {
+                            if (w > *dst) *dst = w;
+                        }
+                        T *= exp(-x);
+                        if (gamma > 0 && T < gamma) break;
+                    }
+                }
+            }
+            free(buf);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Analytic derivatives (App. B.3.2)                                          */
 /* ------------------------------------------------------------------------ */
 

@@ -93,6 +93,8 @@ _SIGS = {
     "pot_loss_mse": [C.c_int64, _p, _p, _p, _p, _p],
     "pot_camera_rays": [_p, C.c_int32, C.c_int64, _p, _p, _p, _p],
     "pot_render_batch": [_p, C.c_int32, _p],
+    "pot_visibility": [_p, _p, C.c_int32, _p, _p, _p],
+    "pot_tree_prune": [_p, _p, C.c_float, _p, _p],
 }
 
 
@@ -271,6 +273,12 @@ class Tree:
 
     def set_values(self, sigma, sh, stream=None):
         _check(lib().pot_tree_set_values(self.handle, _ptr(sigma), _ptr(sh), _stream(stream)))
+
+    def prune(self, score, threshold: float, stream=None) -> "Tree":
+        """``pot_tree_prune``: a new tree of the leaves with score >= threshold (Sec. 3.2 "Filtering")."""
+        out = C.c_void_p()
+        _check(lib().pot_tree_prune(self.handle, _ptr(score), float(threshold), C.byref(out), _stream(stream)))
+        return Tree(out.value)
 
 
 # ----------------------------------------------------------------------------
@@ -463,3 +471,14 @@ def render_batch(items, stream=None):
         r.rgb = rgb.data_ptr()
         r.t_final = None if tf is None else tf.data_ptr()
     _check(lib().pot_render_batch(arr, len(items), _stream(stream)))
+
+
+def visibility(tree: Tree, cams, max_weight=None, gamma=0.0, stream=None):
+    """``pot_visibility``: per-leaf max ray weight over the cameras' pixels (accumulates by max)."""
+    import torch
+    carr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    if max_weight is None:
+        max_weight = torch.zeros(tree.info()["n_leaves"], dtype=torch.float32, device="cuda")
+    o = _opts((0.0, 0.0, 0.0), gamma)
+    _check(lib().pot_visibility(tree.handle, carr, len(carr), C.byref(o), _ptr(max_weight), _stream(stream)))
+    return max_weight

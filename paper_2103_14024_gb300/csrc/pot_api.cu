@@ -657,6 +657,73 @@ pot_status pot_render_rays(const pot_tree *t, int64_t n, const float *origins, c
     return POT_OK;
 }
 
+pot_status pot_visibility(const pot_tree *t, const pot_camera *cams, int32_t n_cams, const pot_render_opts *opts,
+                          float *max_weight, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n_cams < 0) return fail(POT_ERR_INVALID_ARG, "n_cams < 0");
+    if (n_cams == 0 || t->n_leaves == 0) return POT_OK;
+    if (!cams || !max_weight) return fail(POT_ERR_INVALID_ARG, "NULL cams or max_weight");
+    if (is_device_ptr(cams)) return fail(POT_ERR_INVALID_ARG, "cams must be in host memory");
+    if (!is_device_ptr(max_weight)) return fail(POT_ERR_INVALID_ARG, "max_weight must be device memory");
+    pot_status st = check_opts(opts);
+    if (st != POT_OK) return st;
+    if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used here");
+    const int W = cams[0].width, H = cams[0].height;
+    for (int c = 0; c < n_cams; ++c)
+        if (cams[c].width != W || cams[c].height != H || W <= 0 || H <= 0 || !(cams[c].near >= 0.f) ||
+            !std::isfinite(cams[c].fx) || !std::isfinite(cams[c].fy) || cams[c].fx == 0.f || cams[c].fy == 0.f)
+            return fail(POT_ERR_INVALID_ARG, "camera %d invalid or of another size", c);
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp scratch;
+    const size_t cam_off = 256;
+    POT_CUDA(scratch.alloc(cam_off + sizeof(pot_camera) * n_cams, s), "alloc scratch");
+    char *sp = static_cast<char *>(scratch.p);
+    POT_CUDA(cudaMemsetAsync(sp, 0, cam_off, s), "memset");
+    POT_CUDA(cudaMemcpyAsync(sp + cam_off, cams, sizeof(pot_camera) * n_cams, cudaMemcpyHostToDevice, s), "copy cams");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
+    p.n_cams = n_cams;
+    p.view_group = render_view_group(n_cams);
+    p.W = W;
+    p.H = H;
+    p.tiles_x = (W + 7) / 8;
+    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
+    p.n_tiles = p.tiles_per_cam * n_cams;
+    p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
+    POT_CUDA(launch_visibility(p, t, max_weight, s), "visibility");
+    return POT_OK;
+}
+
+pot_status pot_tree_prune(const pot_tree *t, const float *score, float threshold, pot_tree **out, pot_stream stream)
+{
+    if (!t || !out) return fail(POT_ERR_INVALID_ARG, "NULL tree or out");
+    *out = nullptr;
+    if (std::isnan(threshold)) return fail(POT_ERR_INVALID_ARG, "threshold is NaN");
+    if (t->n_leaves > 0 && (!score || !is_device_ptr(score)))
+        return fail(POT_ERR_INVALID_ARG, "score must be device memory");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t *codes = nullptr;
+    float *sig = nullptr, *sh = nullptr;
+    int64_t n = 0;
+    cudaError_t e = compact_kept_leaves(t, score, threshold, &codes, &sig, &sh, &n, s);
+    Tmp fc, fs, fh, tf;
+    fc.p = codes;
+    fc.s = s;
+    fs.p = sig;
+    fs.s = s;
+    fh.p = sh;
+    fh.s = s;
+    if (e != cudaSuccess) return cuda_fail(e, "prune");
+    POT_CUDA(tf.alloc(sizeof(unsigned), s), "alloc flags");
+    POT_CUDA(cudaMemsetAsync(tf.p, 0, sizeof(unsigned), s), "memset");
+    return finish_build(&t->desc, n, codes, sig, sh, static_cast<unsigned *>(tf.p), out, s);
+}
+
 pot_status pot_render_batch(const pot_render_item *items, int32_t n_items, pot_stream stream)
 {
     if (n_items < 0) return fail(POT_ERR_INVALID_ARG, "n_items < 0");

@@ -84,7 +84,7 @@ __global__ void scan_tiles(const int *in, int *out, int64_t n, const int *prefix
         if (base + k < n) out[base + k] = v[k] + off;
 }
 
-cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s)
+cudaError_t scan_inclusive_impl(const int *in, int *out, int64_t n, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
@@ -99,7 +99,7 @@ cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s)
     scan_tile_totals<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, tot);
     count_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = scan_inclusive(tot, tot + tiles, tiles, s);
+    if (e == cudaSuccess) e = scan_inclusive_impl(tot, tot + tiles, tiles, s);
     if (e == cudaSuccess) {
         scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, tot + tiles);
         count_launch();
@@ -284,6 +284,13 @@ __global__ void k_dense_gather(int depth, int K, const float *sigma, const float
 }
 
 }  // namespace
+
+cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s);
+
+cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s)
+{
+    return scan_inclusive_impl(in, out, n, s);
+}
 
 cudaError_t validate_sparse(int depth, int64_t n, const uint64_t *d_codes, const float *d_sigma,
                             unsigned int *d_flags, cudaStream_t s)

@@ -91,6 +91,9 @@ cudaError_t launch_mse(int64_t n, const float *rgb, const float *target, float *
 cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int H, int64_t n, const int64_t *pixels,
                                float *o, float *d, unsigned *d_flag, cudaStream_t s);
 
+cudaError_t launch_visibility(const RenderParams &p, const pot_tree *t, float *max_w, cudaStream_t s);
+cudaError_t compact_kept_leaves(const pot_tree *t, const float *score, float threshold, uint64_t **codes,
+                                float **sig_out, float **sh_out, int64_t *n_keep, cudaStream_t s);
 cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_t s, unsigned int *err);
 
 // cameras interleaved per tile group in camera renders (POT_VIEW_GROUP overrides)
