@@ -598,8 +598,8 @@ pot_status pot_render(const pot_tree *t, const pot_camera *cams, int32_t n_cams,
     if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
     p.W = W;
     p.H = H;
-    p.tiles_x = (W + 7) / 8;
-    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
+    p.tiles_x = (W + kTileW - 1) / kTileW;
+    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
     p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
     const pot_camera *d_cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
     const bool host_out = !is_device_ptr(rgb) || (t_final && !is_device_ptr(t_final));
@@ -690,8 +690,8 @@ pot_status pot_visibility(const pot_tree *t, const pot_camera *cams, int32_t n_c
     p.view_group = render_view_group(n_cams);
     p.W = W;
     p.H = H;
-    p.tiles_x = (W + 7) / 8;
-    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
+    p.tiles_x = (W + kTileW - 1) / kTileW;
+    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
     p.n_tiles = p.tiles_per_cam * n_cams;
     p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
     POT_CUDA(launch_visibility(p, t, max_weight, s), "visibility");

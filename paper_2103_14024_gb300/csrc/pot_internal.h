@@ -23,7 +23,14 @@ struct pot_tree {
     int saturated;
 };
 
+#ifndef POT_TILE_W
+#define POT_TILE_W 4  // pixels per tile row: a warp renders POT_TILE_W x (32 / POT_TILE_W) pixels
+#endif
+
 namespace pot {
+
+constexpr int kTileW = POT_TILE_W;
+constexpr int kTileH = 32 / POT_TILE_W;
 
 // Everything a render launch needs; passed by value.
 struct RenderParams {
@@ -39,7 +46,7 @@ struct RenderParams {
     float bg[3];
     float gamma;
     int step_cap;
-    // ray source: cameras (tiles of 8 x 4 pixels) or explicit rays (32 per tile)
+    // ray source: cameras (tiles of kTileW x kTileH pixels) or explicit rays (32 per tile)
     const pot_camera *cams;
     int n_cams;
     int view_group;     // tiles are interleaved over groups of this many consecutive cameras

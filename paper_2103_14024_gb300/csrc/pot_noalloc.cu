@@ -184,8 +184,8 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
     p.H = H;
     p.n_cams = n_cams;
     p.view_group = render_view_group(n_cams);
-    p.tiles_x = (W + 7) / 8;
-    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + 3) / 4);
+    p.tiles_x = (W + kTileW - 1) / kTileW;
+    p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
     p.n_tiles = p.tiles_per_cam * n_cams;
     p.rgb = rgb;
     p.t_final = t_final;

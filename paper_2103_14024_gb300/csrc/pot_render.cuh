@@ -1,6 +1,6 @@
 // pot_render.cuh -- forward render kernel of the PlenOctree path (sm_103a).
 //
-// One warp renders one tile of 32 rays at a time (8 x 4 pixels of a camera,
+// One warp renders one tile of 32 rays at a time (4 x 8 pixels of a camera,
 // or 32 consecutive explicit rays); warps take tiles from a global counter
 // until none is left (persistent grid, one wave of resident blocks).  Per ray:
 //   a1 pinhole ray (fp32 expression of the public header)
@@ -25,6 +25,13 @@ constexpr int kBlock = 256;
 #ifndef POT_RENDER_MIN_BLOCKS
 #define POT_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
 #endif
+#ifndef POT_PREFETCH
+// prefetch the next cell's leaf into L1 before shading the current one (helped
+// while leaves streamed from DRAM; with neighbouring views sharing L2 it costs
+// 1-2 %, so it is off)
+#define POT_PREFETCH 0
+#endif
+
 
 // One ray's walk through the octree (a2-a4) as resumable state: begin() sets
 // the ray up (clip, locate, first descent), step() advances one cell and calls
@@ -122,7 +129,7 @@ struct Walker {
         lvl_valid = 0;
         stk[0] = 0;
         descend(p, stk, q, q, leaf, cell_lvl);
-        if (leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
+        if (POT_PREFETCH && leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
         // exit plane (voxel index) and crossing time per axis, recomputed only
         // when the plane changes (once per step inside runs of leaves)
 #pragma unroll
@@ -191,7 +198,7 @@ struct Walker {
                     stop = true;
                 } else {
                     descend(p, stk, nq, q, nleaf, nlvl);
-                    if (nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
+                    if (POT_PREFETCH && nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
                 }
             }
         }
@@ -250,7 +257,7 @@ struct ShadeVisitor {
 };
 
 // Ray (origin, direction, clip range, output index) of slot `slot` (0..31) of
-// tile `tile`: 8x4 pixels of a camera (tiles interleaved over groups of
+// tile `tile`: kTileW x kTileH pixels of a camera (tiles interleaved over groups of
 // adjacent cameras) or 32 consecutive explicit rays.  False for slots outside
 // the image or past the last ray.
 template <bool CAMS>
@@ -259,7 +266,7 @@ __device__ __forceinline__ bool tile_ray(const RenderParams &p, unsigned long lo
 {
     if (CAMS) {
         // tiles of a group of G consecutive cameras are interleaved: the same
-        // 8x4 tile of each camera of the group in turn, so neighbouring views
+        // tile of each camera of the group in turn, so neighbouring views
         // (which touch nearly the same leaves) share L1/L2
         const int64_t G = p.view_group;
         const int64_t group = (int64_t)tile / (p.tiles_per_cam * G);
@@ -269,8 +276,8 @@ __device__ __forceinline__ bool tile_ray(const RenderParams &p, unsigned long lo
         const int64_t rem = in_group / gsize;
         const int ty = (int)(rem / p.tiles_x);
         const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
-        const int i = tx * 8 + (slot & 7);
-        const int j = ty * 4 + (slot >> 3);
+        const int i = tx * kTileW + (slot % kTileW);
+        const int j = ty * kTileH + (slot / kTileW);
         if (i >= p.W || j >= p.H) return false;
         ray = (cam * p.H + j) * p.W + i;
         const pot_camera *c = p.cams + cam;
