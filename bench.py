@@ -342,8 +342,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16"])
-    ap.add_argument("--variants", default="f16,bf16", help="extra leaf dtypes to time ('' for none)")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "cb16"])
+    ap.add_argument("--variants", default="f16,bf16,cb16", help="extra leaf dtypes to time ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -388,7 +388,12 @@ def main():
     rays = len(cams) * W * H
 
     def measure(dtype, e2e=False):
-        tree = pot.Tree.from_scene(scene, dtype=dtype)
+        if dtype == "cb16":     # median-cut SH codebooks (2^16 entries per basis) of the f32 tree
+            t32 = pot.Tree.from_scene(scene, dtype="f32")
+            tree = t32.quantize(16)
+            t32.free()
+        else:
+            tree = pot.Tree.from_scene(scene, dtype=dtype)
         info = tree.info()
         rgb = torch.empty((len(cams), H, W, 3), dtype=torch.float32, device="cuda")
 

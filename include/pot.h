@@ -70,7 +70,12 @@ typedef enum pot_status {
 /* Storage type of leaf values (density and SH).  Arithmetic is fp32 always;
  * the paper optimises in float32 and stores the tree in float16 (App. C,
  * PlenOctree optimisation details). */
-typedef enum pot_dtype { POT_F32 = 0, POT_F16 = 1, POT_BF16 = 2 } pot_dtype;
+typedef enum pot_dtype {
+    POT_F32 = 0,
+    POT_F16 = 1,
+    POT_BF16 = 2,
+    POT_CB16 = 3 /* codebook-quantised SH (pot_tree_quantize only): fp16 sigma, uint16 codes */
+} pot_dtype;
 
 typedef struct pot_tree pot_tree;
 
@@ -275,6 +280,20 @@ pot_status pot_visibility(const pot_tree *tree, const pot_camera *cams, int32_t 
  * elsewhere, so empty space grows where leaves were dropped.  Synchronises. */
 pot_status pot_tree_prune(const pot_tree *tree, const float *score, float threshold, pot_tree **out,
                           pot_stream stream);
+
+/* --------------------------------------------------------- quantisation ---
+ * App. B.2: a copy of `tree` whose SH coefficients are quantised, separately
+ * for each SH basis function, into a codebook of 2^bits RGB entries (float16)
+ * by median cut, each leaf keeping one uint16 code per basis function; sigma
+ * is kept, stored as float16.  Median cut here: every box splits at every
+ * level; the split axis is the box's longest extent (ties: lowest channel);
+ * its points are ordered by (value on that axis, leaf index) and split at
+ * floor(n/2); a box of fewer than two points keeps them.  An entry is the mean
+ * of its box (float64, summed in box order, rounded once to float16).  The
+ * result has leaf_dtype POT_CB16; it renders, batches, filters and exports
+ * (values = the codebook entries) like any tree; no gradients or set_values.
+ * bits: 1..16.  Runs on the host (threads over basis functions); synchronises. */
+pot_status pot_tree_quantize(const pot_tree *tree, int32_t bits, pot_tree **out, pot_stream stream);
 
 /* ---------------------------------------------------------------- batch ---
  * Many render requests in one call -- the work list of a continuous-batching

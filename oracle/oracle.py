@@ -306,3 +306,74 @@ def step_adam(x, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** step)
     vh = v / (1.0 - beta2 ** step)
     return x - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ----------------------------------------------------------------------------
+# SH codebook quantisation (App. B.2): median cut per SH basis function
+# ----------------------------------------------------------------------------
+
+def median_cut(points, bits: int):
+    """Median-cut quantisation (Heckbert) of float32 points [n, 3] into 2^bits
+    boxes, every box split at every level: the split axis is the box's longest
+    extent (ties: lowest channel); the box's points are ordered by (value on
+    that axis, point index) and split at floor(n/2); boxes of fewer than two
+    points keep them and get an empty sibling.  Returns (codebook float16
+    [2^bits, 3] = the fp64 mean of each box in box order rounded once to fp16,
+    0 for empty boxes; codes uint16 [n])."""
+    P = np.asarray(points, dtype=np.float32)
+    n = P.shape[0]
+    order = np.arange(n, dtype=np.int64)
+    starts = np.array([0], dtype=np.int64)
+    ends = np.array([n], dtype=np.int64)
+    for _ in range(bits):
+        sizes = ends - starts
+        box_of = np.repeat(np.arange(starts.shape[0]), sizes)
+        vals = P[order].astype(np.float64)
+        big = sizes >= 2
+        # per-box extents (boxes with >= 1 point)
+        nz = sizes > 0
+        mx = np.full((starts.shape[0], 3), -np.inf)
+        mn = np.full((starts.shape[0], 3), np.inf)
+        if n:
+            mx[nz] = np.maximum.reduceat(vals, starts[nz], axis=0)
+            mn[nz] = np.minimum.reduceat(vals, starts[nz], axis=0)
+        axis = np.argmax(np.where(nz[:, None], mx - mn, -1.0), axis=1)
+        key = vals[np.arange(n), axis[box_of]] if n else vals[:, 0]
+        # sort inside boxes that split: by (box, value on the box's axis, point index)
+        key = np.where(big[box_of], key, 0.0)
+        perm = np.lexsort((order, key, box_of))
+        order = order[perm]
+        mids = starts + sizes // 2
+        mids = np.where(big, mids, ends)
+        new_s = np.stack([starts, mids], axis=1).reshape(-1)
+        new_e = np.stack([mids, ends], axis=1).reshape(-1)
+        starts, ends = new_s, new_e
+    C = starts.shape[0]
+    codebook = np.zeros((C, 3), dtype=np.float16)
+    codes = np.zeros(n, dtype=np.uint16)
+    for j in range(C):
+        s, e = starts[j], ends[j]
+        if e > s:
+            idx = order[s:e]
+            acc = np.zeros(3)
+            for i in idx:                       # sequential fp64 sum in box order
+                acc = acc + P[i].astype(np.float64)
+            codebook[j] = (acc / (e - s)).astype(np.float16)
+            codes[idx] = j
+    return codebook, codes
+
+
+def quantize_scene(scene, bits: int):
+    """The scene with sigma rounded to float16 and each SH basis function's RGB
+    coefficients replaced by their median-cut codebook entries (float16),
+    i.e. the values a quantised tree stores; also the codebooks and codes."""
+    K = scene.sh_dim
+    sh = np.empty_like(scene.sh)
+    books, codes = [], []
+    for k in range(K):
+        cb, cd = median_cut(scene.sh[:, k, :], bits)
+        sh[:, k, :] = cb[cd].astype(np.float32)
+        books.append(cb)
+        codes.append(cd)
+    sig, _ = round_values(scene.sigma, "f16")
+    return scene.replace(sigma=sig, sh=sh), np.stack(books), np.stack(codes, axis=1)

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "libpot.so")
 
 POT_OK, POT_ERR_INVALID_ARG, POT_ERR_OOM, POT_ERR_CUDA, POT_ERR_TRAVERSAL, POT_ERR_BUDGET, \
     POT_ERR_UNSUPPORTED = range(7)
-DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+DTYPES = {"f32": 0, "f16": 1, "bf16": 2, "cb16": 3}
 _STATUS = {0: "POT_OK", 1: "POT_ERR_INVALID_ARG", 2: "POT_ERR_OOM", 3: "POT_ERR_CUDA",
            4: "POT_ERR_TRAVERSAL", 5: "POT_ERR_BUDGET", 6: "POT_ERR_UNSUPPORTED"}
 
@@ -95,6 +95,7 @@ _SIGS = {
     "pot_render_batch": [_p, C.c_int32, _p],
     "pot_visibility": [_p, _p, C.c_int32, _p, _p, _p],
     "pot_tree_prune": [_p, _p, C.c_float, _p, _p],
+    "pot_tree_quantize": [_p, C.c_int32, _p, _p],
 }
 
 
@@ -273,6 +274,12 @@ class Tree:
 
     def set_values(self, sigma, sh, stream=None):
         _check(lib().pot_tree_set_values(self.handle, _ptr(sigma), _ptr(sh), _stream(stream)))
+
+    def quantize(self, bits: int = 16, stream=None) -> "Tree":
+        """``pot_tree_quantize``: median-cut SH codebooks of 2^bits entries per basis function (App. B.2)."""
+        out = C.c_void_p()
+        _check(lib().pot_tree_quantize(self.handle, int(bits), C.byref(out), _stream(stream)))
+        return Tree(out.value)
 
     def prune(self, score, threshold: float, stream=None) -> "Tree":
         """``pot_tree_prune``: a new tree of the leaves with score >= threshold (Sec. 3.2 "Filtering")."""

@@ -202,6 +202,7 @@ void destroy_tree(pot_tree *t)
     cudaFree(t->sigma);
     cudaFree(t->sh);
     cudaFree(t->morton);
+    cudaFree(t->codebook);
     delete t;
 }
 
@@ -261,6 +262,7 @@ void fill_tree_params(RenderParams &p, const pot_tree *t, const pot_render_opts 
     p.child = t->child;
     p.sigma = t->sigma;
     p.sh = t->sh;
+    p.codebook = t->codebook;
     p.depth = t->desc.depth;
     p.R = 1 << t->desc.depth;
     for (int a = 0; a < 3; ++a) p.lo[a] = t->desc.bbox_lo[a];
@@ -284,6 +286,7 @@ cudaError_t launch_render(const RenderParams &p, const pot_tree *t, bool cams, c
     switch (t->desc.leaf_dtype) {
     case POT_F32: return launch_render_f32(p, t->K, cams, count, s, 0);
     case POT_F16: return launch_render_f16(p, t->K, cams, count, s, 0);
+    case POT_CB16: return launch_render_cb16(p, t->K, cams, count, s, 0);
     default: return launch_render_bf16(p, t->K, cams, count, s, 0);
     }
 }
@@ -460,7 +463,7 @@ pot_status pot_tree_get_info(const pot_tree *t, pot_tree_info *info)
     info->n_nodes = t->n_nodes;
     info->n_leaves = t->n_leaves;
     info->bytes = t->bytes;
-    info->leaf_bytes = (int64_t)t->elem_bytes * (1 + t->stride);
+    info->leaf_bytes = (int64_t)t->elem_bytes * (1 + t->stride);  // cb16: fp16 sigma + uint16 codes
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = t->desc.bbox_lo[a];
     info->bbox_size = t->desc.bbox_size;
     info->saturated = t->saturated;
@@ -497,6 +500,7 @@ pot_status pot_tree_set_values(pot_tree *t, const float *sigma, const float *sh,
     if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
     if (t->n_leaves == 0) return POT_OK;
     if (!sigma || !sh) return fail(POT_ERR_INVALID_ARG, "NULL input array");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "codebook leaves are read-only");
     DeviceGuard g(t->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n_leaves;
@@ -724,6 +728,43 @@ pot_status pot_tree_prune(const pot_tree *t, const float *score, float threshold
     return finish_build(&t->desc, n, codes, sig, sh, static_cast<unsigned *>(tf.p), out, s);
 }
 
+pot_status pot_tree_quantize(const pot_tree *t, int32_t bits, pot_tree **out, pot_stream stream)
+{
+    if (!t || !out) return fail(POT_ERR_INVALID_ARG, "NULL tree or out");
+    *out = nullptr;
+    if (bits < 1 || bits > 16) return fail(POT_ERR_INVALID_ARG, "bits must be in 1..16");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "tree is already quantised");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pot_tree *q = new (std::nothrow) pot_tree();
+    if (!q) return fail(POT_ERR_OOM, "host allocation failed");
+    *q = *t;
+    q->desc.leaf_dtype = POT_CB16;
+    q->stride = cb_stride(t->K);
+    q->elem_bytes = 2;
+    q->child = nullptr;
+    q->sigma = nullptr;
+    q->sh = nullptr;
+    q->morton = nullptr;
+    q->codebook = nullptr;
+    cudaError_t e = cudaMalloc(&q->child, sizeof(int32_t) * 8 * t->n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&q->morton, sizeof(uint64_t) * (t->n_leaves > 0 ? t->n_leaves : 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(q->child, t->child, sizeof(int32_t) * 8 * t->n_nodes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && t->n_leaves > 0)
+        e = cudaMemcpyAsync(q->morton, t->morton, sizeof(uint64_t) * t->n_leaves, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = quantize_tree(t, bits, q, s);
+    if (e != cudaSuccess) {
+        destroy_tree(q);
+        return cuda_fail(e, "quantize");
+    }
+    const int64_t n = t->n_leaves;
+    q->bytes = q->n_nodes * 32 + n * 8 + ((n * 2 + 255) / 256) * 256 + n * (int64_t)q->stride * 2 +
+               (int64_t)t->K * 65536 * 8;
+    *out = q;
+    return POT_OK;
+}
+
 pot_status pot_render_batch(const pot_render_item *items, int32_t n_items, pot_stream stream)
 {
     if (n_items < 0) return fail(POT_ERR_INVALID_ARG, "n_items < 0");
@@ -767,6 +808,7 @@ pot_status pot_render_backward(const pot_tree *t, int64_t n, const float *origin
     pot_status st = check_opts(opts);
     if (st != POT_OK) return st;
     if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
     const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
     if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
     DeviceGuard g(t->device);

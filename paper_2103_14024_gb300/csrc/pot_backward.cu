@@ -49,7 +49,7 @@ struct GradVisitor {
         const float sraw = Store<T>::load_sigma(sig_arr, leaf);
         const float sig = fmaxf(sraw, 0.f);
         float x[3];
-        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
+        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x, nullptr);
         const float e = __expf(-sig * delta);  // same operations as the forward
         const float w = Tr * (1.f - e);
         const float Tn = Tr * e;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(bp.rgb_fwd + 3 * ray + c);
             } else {
-                ShadeVisitor<K, T, false> sv{sig_arr, sh_arr, nullptr, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
+                ShadeVisitor<K, T, false> sv{sig_arr, sh_arr, nullptr, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0, nullptr};
                 walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, p.near, p.far, sv);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = fmaf(sv.Tr, p.bg[c], sv.col[c]);

@@ -19,6 +19,7 @@ struct BatchItem {
     const int32_t *child;
     const void *sigma;
     const void *sh;
+    const void *codebook;
     int depth, R;
     float lo[3];
     float size, h, invh;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
             }
             const T *sig_arr = static_cast<const T *>(it.sigma);
             const T *sh_arr = static_cast<const T *>(it.sh);
-            ShadeVisitor<K, T, false> v{sig_arr, sh_arr, nullptr, it.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
+            ShadeVisitor<K, T, false> v{sig_arr, sh_arr, nullptr, it.gamma, {0.f, 0.f, 0.f}, 1.f, 0, it.codebook};
             walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, c->near, c->far, v);
             const int64_t px = (int64_t)j * it.W + i;
 #pragma unroll
@@ -143,6 +144,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         b.child = t->child;
         b.sigma = t->sigma;
         b.sh = t->sh;
+        b.codebook = t->codebook;
         b.depth = t->desc.depth;
         b.R = 1 << t->desc.depth;
         for (int a = 0; a < 3; ++a) b.lo[a] = t->desc.bbox_lo[a];
@@ -184,6 +186,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         switch (t->desc.leaf_dtype) {
         case POT_F32: e = launch_batch_t<float>(bp, t->K, s); break;
         case POT_F16: e = launch_batch_t<__half>(bp, t->K, s); break;
+        case POT_CB16: e = launch_batch_t<cb16>(bp, t->K, s); break;
         default: e = launch_batch_t<__nv_bfloat16>(bp, t->K, s); break;
         }
     }

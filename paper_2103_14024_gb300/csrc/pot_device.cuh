@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pot {
 
 constexpr int kMaxDepth = 12;
@@ -240,18 +242,36 @@ struct Store<__nv_bfloat16> {
     }
 };
 
+// Codebook-quantised leaves (App. B.2): sigma as fp16 [L]; per leaf one uint16
+// code per SH basis function, the record padded to 16 bytes; per basis
+// function a codebook of 65536 entries of 4 fp16 (R, G, B, 0).
+struct cb16 {
+};
+constexpr int kCodebookEntries = 65536;
+
+template <>
+struct Store<cb16> {
+    static constexpr int kVec = 8;  // codes per 16-byte load
+    __device__ static __forceinline__ float load_sigma(const cb16 *s, int64_t i)
+    {
+        return __half2float(__ldg(reinterpret_cast<const __half *>(s) + i));
+    }
+};
+
 // Elements per padded SH record for K coefficients per channel.
 template <typename T>
 __host__ __device__ constexpr int sh_stride(int K)
 {
     return (3 * K + Store<T>::kVec - 1) / Store<T>::kVec * Store<T>::kVec;
 }
+// codebook leaves: K codes (uint16) per record
+__host__ __device__ constexpr int cb_stride(int K) { return (K + 7) / 8 * 8; }
 
 // x_c = sum_k sh[k][c] Y_k for the three channels of one leaf; the record is
 // read in chunks of up to four 16-byte loads to bound live registers (the
 // lines were prefetched into L1 a step earlier).
 template <int K, typename T>
-__device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const float *Y, float *x)
+__device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const float *Y, float *x, const void *)
 {
     constexpr int V = Store<T>::kVec;
     constexpr int N = 3 * K;
@@ -280,15 +300,54 @@ __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const flo
     }
 }
 
+// Codebook leaves: x_c = sum_k codebook[k][code_k][c] Y_k.
+template <int K>
+__device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, const float *Y, float *x, const void *cb)
+{
+    constexpr int NV = (K + 7) / 8;
+    const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint16_t *>(sh) + leaf * (int64_t)(NV * 8));
+    const uint2 *book = static_cast<const uint2 *>(cb);
+    uint4 raw[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) raw[v] = __ldg(p + v);
+    uint2 e[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint4 r = raw[k / 8];
+        const uint32_t w = (k % 8) / 2 == 0 ? r.x : (k % 8) / 2 == 1 ? r.y : (k % 8) / 2 == 2 ? r.z : r.w;
+        const uint32_t code = (k & 1) ? (w >> 16) : (w & 0xFFFFu);
+        e[k] = __ldg(book + (int64_t)k * kCodebookEntries + code);
+    }
+    x[0] = x[1] = x[2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&e[k].x));
+        const float b = __half2float(__ushort_as_half((unsigned short)(e[k].y & 0xFFFFu)));
+        x[0] = fmaf(rg.x, Y[k], x[0]);
+        x[1] = fmaf(rg.y, Y[k], x[1]);
+        x[2] = fmaf(b, Y[k], x[2]);
+    }
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void leaf_colour_dot(const T *sh, int64_t leaf, const float *Y, float *x, const void *cb)
+{
+    if constexpr (std::is_same<T, cb16>::value) leaf_sh_dot_cb<K>(sh, leaf, Y, x, cb);
+    else leaf_sh_dot<K, T>(sh, leaf, Y, x, cb);
+}
+
 // Ask L1 for the lines of one leaf (SH record and sigma) ahead of its use.
 template <int K, typename T>
 __device__ __forceinline__ void prefetch_leaf(const T *sig, const T *sh, int64_t leaf)
 {
+    if constexpr (std::is_same<T, cb16>::value) return;
+    else {
     constexpr int bytes = sh_stride<T>(K) * (int)sizeof(T);
     const char *r = reinterpret_cast<const char *>(sh + leaf * (int64_t)sh_stride<T>(K));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(r));
     if (bytes > 16) asm volatile("prefetch.global.L1 [%0];" ::"l"(r + bytes - 1));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(sig + leaf));
+    }
 }
 
 // 1 / (1 + e^-x); x is clamped at -80 (sigmoid < 2e-35) so the divisor stays

@@ -122,6 +122,7 @@ cudaError_t launch_visibility(const RenderParams &p, const pot_tree *t, float *m
     switch (t->desc.leaf_dtype) {
     case POT_F32: return launch_visibility_t<float>(p, t->K, max_w, s);
     case POT_F16: return launch_visibility_t<__half>(p, t->K, max_w, s);
+    case POT_CB16: return launch_visibility_t<cb16>(p, t->K, max_w, s);
     default: return launch_visibility_t<__nv_bfloat16>(p, t->K, max_w, s);
     }
 }

@@ -21,6 +21,8 @@ struct pot_tree {
     uint64_t *morton;   // [n_leaves]
     int64_t bytes;
     int saturated;
+    void *codebook;     // POT_CB16: [K][65536][4] fp16
+    int cb_bits;        // POT_CB16: codebook entries used per basis function = 2^cb_bits
 };
 
 #ifndef POT_TILE_W
@@ -37,6 +39,7 @@ struct RenderParams {
     const int32_t *child;
     const void *sigma;
     const void *sh;
+    const void *codebook;  // POT_CB16 trees
     int depth;
     int R;
     float lo[3];
@@ -75,6 +78,8 @@ cudaError_t launch_render_f16(const RenderParams &p, int K, bool cams, bool coun
                               int max_blocks);
 cudaError_t launch_render_bf16(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
                                int max_blocks);
+cudaError_t launch_render_cb16(const RenderParams &p, int K, bool cams, bool count, cudaStream_t s,
+                               int max_blocks);
 
 // Build / query / export helpers (pot_build.cu, pot_query.cu).
 cudaError_t build_levels_and_children(pot_tree *t, int64_t n, const uint64_t *d_codes, cudaStream_t s,
@@ -101,6 +106,7 @@ cudaError_t launch_camera_rays(const pot_camera *d_cams, int n_cams, int W, int 
 cudaError_t launch_visibility(const RenderParams &p, const pot_tree *t, float *max_w, cudaStream_t s);
 cudaError_t compact_kept_leaves(const pot_tree *t, const float *score, float threshold, uint64_t **codes,
                                 float **sig_out, float **sh_out, int64_t *n_keep, cudaStream_t s);
+cudaError_t quantize_tree(const pot_tree *t, int bits, pot_tree *q, cudaStream_t s);
 cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_t s, unsigned int *err);
 
 // cameras interleaved per tile group in camera renders (POT_VIEW_GROUP overrides)

@@ -164,6 +164,7 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
     p.child = t->child;
     p.sigma = t->sigma;
     p.sh = t->sh;
+    p.codebook = t->codebook;
     p.depth = t->desc.depth;
     p.R = 1 << t->desc.depth;
     for (int a = 0; a < 3; ++a) p.lo[a] = t->desc.bbox_lo[a];
@@ -194,6 +195,7 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
     switch (t->desc.leaf_dtype) {
     case POT_F32: e = launch_render_f32(p, t->K, true, count, s, 0); break;
     case POT_F16: e = launch_render_f16(p, t->K, true, count, s, 0); break;
+    case POT_CB16: e = launch_render_cb16(p, t->K, true, count, s, 0); break;
     default: e = launch_render_bf16(p, t->K, true, count, s, 0); break;
     }
     if (e != cudaSuccess) return na_cuda(e, "render launch");

@@ -238,11 +238,12 @@ struct ShadeVisitor {
     float col[3];
     float Tr;
     int nseg;
+    const void *cb;  // codebook (cb16 leaves only)
     __device__ __forceinline__ bool operator()(int leaf, float delta, const float *Y)
     {
         const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
         float x[3];
-        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x);
+        leaf_colour_dot<K, T>(sh_arr, leaf, Y, x, cb);
         const float e = __expf(-sig * delta);  // transmittance of the segment
         const float w = Tr * (1.f - e);
 #pragma unroll
@@ -332,7 +333,8 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
         float o[3], d[3], near, far;
         int64_t ray;
         if (tile_ray<CAMS>(p, tile, lane, o, d, near, far, ray)) {
-            ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0};
+            ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0,
+                                        p.codebook};
             walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, near, far, v);
             store_ray<K, T, COUNT>(p, ray, v);
         }
