@@ -35,8 +35,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 1.5538 GB read + 0.1091 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "6cb1ba2d30a35ec3", "bytes_per_launch": 20.79e9},
+    # 16-view capture (one view group): 1.5504 GB read + 0.1125 GB written, x 12.5 = 200-view launch
+    "f32": {"sha": "243fe1ea203629b4", "bytes_per_launch": 20.78e9},
 }
 
 

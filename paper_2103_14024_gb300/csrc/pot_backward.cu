@@ -44,7 +44,8 @@ struct GradVisitor {
     float Tr;
     float *grad_sigma;
     float *grad_sh;
-    __device__ __forceinline__ bool operator()(int leaf, float delta, const float *Y)
+    template <typename YT>
+    __device__ __forceinline__ bool operator()(int leaf, float delta, const YT &Y)
     {
         const float sraw = Store<T>::load_sigma(sig_arr, leaf);
         const float sig = fmaxf(sraw, 0.f);
@@ -92,8 +93,7 @@ struct BackwardParams {
 template <int K, typename T, bool HAVE_FWD>
 __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kernel(const BackwardParams bp)
 {
-    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
-    int32_t *stk = &stk_sh[0][threadIdx.x];
+    POT_WALK_SHARED(K)
     const RenderParams &p = bp.r;
     const int lane = threadIdx.x & 31;
     const T *sig_arr = static_cast<const T *>(p.sigma);
@@ -128,12 +128,12 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(bp.rgb_fwd + 3 * ray + c);
             } else {
                 ShadeVisitor<K, T, false> sv{sig_arr, sh_arr, nullptr, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0, nullptr};
-                walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, p.near, p.far, sv);
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, p.near, p.far, sv);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = fmaf(sv.Tr, p.bg[c], sv.col[c]);
             }
             if (gv.g[0] != 0.f || gv.g[1] != 0.f || gv.g[2] != 0.f)
-                walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, p.near, p.far, gv);
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, p.near, p.far, gv);
         }
     }
 }

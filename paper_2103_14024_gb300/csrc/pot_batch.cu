@@ -43,8 +43,7 @@ struct BatchParams {
 template <int K, typename T>
 __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(const BatchParams bp)
 {
-    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
-    int32_t *stk = &stk_sh[0][threadIdx.x];
+    POT_WALK_SHARED(K)
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long tile = 0;
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
             const T *sig_arr = static_cast<const T *>(it.sigma);
             const T *sh_arr = static_cast<const T *>(it.sh);
             ShadeVisitor<K, T, false> v{sig_arr, sh_arr, nullptr, it.gamma, {0.f, 0.f, 0.f}, 1.f, 0, it.codebook};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, c->near, c->far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, c->near, c->far, v);
             const int64_t px = (int64_t)j * it.W + i;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) it.rgb[3 * px + ch] = fmaf(v.Tr, it.bg[ch], v.col[ch]);

@@ -270,8 +270,16 @@ __host__ __device__ constexpr int cb_stride(int K) { return (K + 7) / 8 * 8; }
 // x_c = sum_k sh[k][c] Y_k for the three channels of one leaf; the record is
 // read in chunks of up to four 16-byte loads to bound live registers (the
 // lines were prefetched into L1 a step earlier).
-template <int K, typename T>
-__device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const float *Y, float *x, const void *)
+// The per-ray SH basis, either in registers (a plain array) or in shared
+// memory with one column per thread (stride = threads per block).
+template <int STRIDE>
+struct SmemY {
+    const float *base;
+    __device__ __forceinline__ float operator[](int k) const { return base[k * STRIDE]; }
+};
+
+template <int K, typename T, typename YT>
+__device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const YT &Y, float *x, const void *)
 {
     constexpr int V = Store<T>::kVec;
     constexpr int N = 3 * K;
@@ -301,8 +309,8 @@ __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const flo
 }
 
 // Codebook leaves: x_c = sum_k codebook[k][code_k][c] Y_k.
-template <int K>
-__device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, const float *Y, float *x, const void *cb)
+template <int K, typename YT>
+__device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, const YT &Y, float *x, const void *cb)
 {
     constexpr int NV = (K + 7) / 8;
     const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint16_t *>(sh) + leaf * (int64_t)(NV * 8));
@@ -329,8 +337,8 @@ __device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, con
     }
 }
 
-template <int K, typename T>
-__device__ __forceinline__ void leaf_colour_dot(const T *sh, int64_t leaf, const float *Y, float *x, const void *cb)
+template <int K, typename T, typename YT>
+__device__ __forceinline__ void leaf_colour_dot(const T *sh, int64_t leaf, const YT &Y, float *x, const void *cb)
 {
     if constexpr (std::is_same<T, cb16>::value) leaf_sh_dot_cb<K>(sh, leaf, Y, x, cb);
     else leaf_sh_dot<K, T>(sh, leaf, Y, x, cb);

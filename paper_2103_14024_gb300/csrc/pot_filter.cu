@@ -16,7 +16,8 @@ struct MaxWeightVisitor {
     float gamma;
     float Tr;
     float *max_w;
-    __device__ __forceinline__ bool operator()(int leaf, float delta, const float *)
+    template <typename YT>
+    __device__ __forceinline__ bool operator()(int leaf, float delta, const YT &)
     {
         const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
         const float e = __expf(-sig * delta);
@@ -30,8 +31,7 @@ struct MaxWeightVisitor {
 template <int K, typename T>
 __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) visibility_kernel(const RenderParams p, float *max_w)
 {
-    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
-    int32_t *stk = &stk_sh[0][threadIdx.x];
+    POT_WALK_SHARED(K)
     const int lane = threadIdx.x & 31;
     const T *sig_arr = static_cast<const T *>(p.sigma);
     const T *sh_arr = static_cast<const T *>(p.sh);
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) visibility_kern
         int64_t ray;
         if (tile_ray<true>(p, tile, lane, o, d, near, far, ray)) {
             MaxWeightVisitor<T> v{sig_arr, p.gamma, 1.f, max_w};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, near, far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, near, far, v);
         }
     }
 }

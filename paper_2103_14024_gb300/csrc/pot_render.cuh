@@ -23,7 +23,12 @@ namespace pot {
 
 constexpr int kBlock = 256;
 #ifndef POT_RENDER_MIN_BLOCKS
-#define POT_RENDER_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
+#define POT_RENDER_MIN_BLOCKS 4  // resident blocks per SM the register budget is cut for (64 registers)
+#endif
+#ifndef POT_Y_SMEM
+// keep the per-ray SH basis in shared memory instead of registers: frees 16
+// registers per thread, which lets 4 blocks (32 warps) reside per SM
+#define POT_Y_SMEM 1
 #endif
 #ifndef POT_PREFETCH
 // prefetch the next cell's leaf into L1 before shading the current one (helped
@@ -43,7 +48,13 @@ template <int K, typename T>
 struct Walker {
     float d[3], rd[3], Ahi[3], Alo[3], margin[3];
     float len;
-    float Y[K];
+#if POT_Y_SMEM
+    float *ysm;  // this thread's column of the block's [K][kBlock] shared array
+    __device__ __forceinline__ SmemY<kBlock> Y() const { return {ysm}; }
+#else
+    float Yr[K];
+    __device__ __forceinline__ const float *Y() const { return Yr; }
+#endif
     df t, tout;
     int q[3];
     int leaf, cell_lvl, lvl_valid, step_i;
@@ -88,7 +99,16 @@ struct Walker {
         len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
         if (!(len > 0.f) || !(len < 3.0e38f)) return false;
         const float invlen = __frcp_rn(len);
-        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y);
+#if POT_Y_SMEM
+        {
+            float Yt[K];
+            sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Yt);
+#pragma unroll
+            for (int k = 0; k < K; ++k) ysm[k * kBlock] = Yt[k];
+        }
+#else
+        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Yr);
+#endif
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
@@ -203,7 +223,7 @@ struct Walker {
             }
         }
         if (leaf >= 0 && dt > 0.f) {
-            if (vis(leaf, dt * len, Y)) return false;
+            if (vis(leaf, dt * len, Y())) return false;
         }
         if (stop) return false;
 #pragma unroll
@@ -216,13 +236,27 @@ struct Walker {
     }
 };
 
+// Per-thread scratch of a walk in shared memory: the ancestor stack and (with
+// POT_Y_SMEM) the SH basis.  Declared once per kernel.
+#define POT_WALK_SHARED(K)                                          \
+    __shared__ int32_t stk_sh[kMaxDepth][kBlock];                   \
+    __shared__ float ysm_sh[POT_Y_SMEM ? (K) : 1][kBlock];          \
+    int32_t *stk = &stk_sh[0][threadIdx.x];                         \
+    float *ysm = &ysm_sh[0][threadIdx.x];                           \
+    (void)ysm;
+
 // The whole walk of one ray.
 template <int K, typename T, typename Visitor>
 __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
-                                         int32_t *stk, const float o[3], const float d[3], float near,
-                                         float far, Visitor &vis)
+                                         int32_t *stk, float *ysm, const float o[3], const float d[3],
+                                         float near, float far, Visitor &vis)
 {
     Walker<K, T> w;
+#if POT_Y_SMEM
+    w.ysm = ysm;
+#else
+    (void)ysm;
+#endif
     if (!w.begin(p, stk, sig_arr, sh_arr, o, d, near, far)) return;
     while (w.step(p, stk, sig_arr, sh_arr, vis)) {
     }
@@ -239,7 +273,8 @@ struct ShadeVisitor {
     float Tr;
     int nseg;
     const void *cb;  // codebook (cb16 leaves only)
-    __device__ __forceinline__ bool operator()(int leaf, float delta, const float *Y)
+    template <typename YT>
+    __device__ __forceinline__ bool operator()(int leaf, float delta, const YT &Y)
     {
         const float sig = fmaxf(Store<T>::load_sigma(sig_arr, leaf), 0.f);
         float x[3];
@@ -320,8 +355,7 @@ __device__ __forceinline__ void store_ray(const RenderParams &p, int64_t ray, co
 template <int K, typename T, bool CAMS, bool COUNT>
 __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(const RenderParams p)
 {
-    __shared__ int32_t stk_sh[kMaxDepth][kBlock];
-    int32_t *stk = &stk_sh[0][threadIdx.x];
+    POT_WALK_SHARED(K)
     const int lane = threadIdx.x & 31;
     const T *sig_arr = static_cast<const T *>(p.sigma);
     const T *sh_arr = static_cast<const T *>(p.sh);
@@ -335,7 +369,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
         if (tile_ray<CAMS>(p, tile, lane, o, d, near, far, ray)) {
             ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0,
                                         p.codebook};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, o, d, near, far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, near, far, v);
             store_ray<K, T, COUNT>(p, ray, v);
         }
     }
