@@ -466,7 +466,9 @@ def main():
         line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * len(cams),
                        "d2h_bytes_per_step": 12 * rays}
     variants = {}
-    for vd in [v for v in args.variants.split(",") if v and v != args.dtype]:
+    # per-GPU characteristics (other leaf types, training, serving) are measured at N = 1 only
+    extras = world == 1
+    for vd in [v for v in args.variants.split(",") if v and v != args.dtype and extras]:
         r = measure(vd)
         w = r["wall"]
         vb = algorithmic_bytes(pot, torch, r["tree"], cams, vd, int(r["info"]["leaf_bytes"]))
@@ -482,15 +484,16 @@ def main():
         r["tree"].free()
     if variants:
         line["variants"] = variants
-    if not args.no_train:
+    if not args.no_train and extras:
         line["train"] = train_measure(pot, torch, synth, scene, main_res["tree"], args, barrier)
-    if not args.no_serve:
+    if not args.no_serve and extras:
         line["serve"] = serve_measure(pot, torch, synth, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         views = [0, 25, 50, 75, 100, 125, 150, 175]
-        rate, n, dt, thr = run_oracle_timing(scene, cams, views, 2)
+        rate, n, dt, thr = run_oracle_timing(scene, synth.cameras_main(N_VIEWS, W, H), views, 1)
         line["cpu_baseline"] = {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"every 2nd pixel of views 0,25,...,175 ({n} rays, {dt:.1f} s)"}
+                                "sample": f"all pixels of views 0,25,...,175 of 200 ({n} rays, {dt:.1f} s on "
+                                          f"{thr} threads)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -68,7 +68,7 @@ typedef enum pot_status {
 } pot_status;
 
 /* Storage type of leaf values (density and SH).  Arithmetic is fp32 always;
- * the paper optimises in float32 and stores the tree in float16 (App. C,
+ * the paper optimises in float32 and stores the tree in float16 (App. B.5,
  * PlenOctree optimisation details). */
 typedef enum pot_dtype {
     POT_F32 = 0,
@@ -203,7 +203,7 @@ pot_status pot_render_backward(const pot_tree *tree, int64_t n, const float *ori
                                float *grad_sigma, float *grad_sh, pot_stream stream);
 
 /* ----------------------------------------------------------------- step ---
- * Sec. 3.3 / App. C: gradient step on the leaf values with the structure
+ * Sec. 3.3 / App. B.5: gradient step on the leaf values with the structure
  * fixed (the paper uses SGD; RMSprop and Adam are offered too), in place on a
  * float32 tree (other dtypes: POT_ERR_UNSUPPORTED).  Element-wise, separate
  * learning rates for sigma and SH:

@@ -2,7 +2,7 @@
 quantised tree's stored values equal the oracle's median cut bit for bit, its
 renders match the oracle on those values within 1e-4, it batches and filters
 like other trees, and on the main scene its size and image error against the
-float32 tree are recorded (gpurun_out/codebook.json)."""
+float32 tree are recorded (also in $POT_REPORT_DIR/codebook.json when set)."""
 import json
 import math
 import os
@@ -80,8 +80,10 @@ def test_codebook_main_scene(pot):
            "max_abs_vs_f32": float(err.max().item()),
            "psnr_vs_f32_db": 10 * math.log10(1.0 / mse) if mse > 0 else float("inf")}
     print(json.dumps(rep, indent=1))
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "codebook.json"), "w") as f:
-        json.dump(rep, f, indent=1)
+    out_dir = os.environ.get("POT_REPORT_DIR")
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        with open(os.path.join(out_dir, "codebook.json"), "w") as f:
+            json.dump(rep, f, indent=1)
     assert rep["psnr_vs_f32_db"] > 30
     pot.check()

@@ -2,7 +2,7 @@
 per-leaf max ray weights within 1e-4, pruning bit-exact (both sides get the
 same scores, so the threshold decision is shared), renders of the filter views
 unchanged when only never-composited leaves are dropped, and the size/error
-trade-off of tau_w on the main scene (written to gpurun_out/filter.json)."""
+trade-off of tau_w on the main scene (also written to $POT_REPORT_DIR/filter.json when that is set)."""
 import json
 import math
 import os
@@ -105,8 +105,10 @@ def test_filter_main_scene_tradeoff(pot):
                                "psnr_vs_unfiltered_db": 10 * math.log10(1.0 / mse) if mse > 0 else float("inf")}
         tp.free()
     print(json.dumps(rep, indent=1))
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open(os.path.join("gpurun_out", "filter.json"), "w") as f:
-        json.dump(rep, f, indent=1)
+    out_dir = os.environ.get("POT_REPORT_DIR")
+    if out_dir:
+        os.makedirs(out_dir, exist_ok=True)
+        with open(os.path.join(out_dir, "filter.json"), "w") as f:
+            json.dump(rep, f, indent=1)
     assert rep["tau_w=0.001"]["leaves"] <= n0
     pot.check()
