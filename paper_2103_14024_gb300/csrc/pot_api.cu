@@ -240,6 +240,11 @@ pot_status finish_build(const pot_build_desc *desc, int64_t n, const uint64_t *d
     return POT_OK;
 }
 
+pot_status tile_limit_error()
+{
+    return fail(POT_ERR_INVALID_ARG, "too many pixels in one call (tiles must stay below 2^32): split the cameras");
+}
+
 pot_status check_opts(const pot_render_opts *o)
 {
     if (!o) return POT_OK;
@@ -604,6 +609,8 @@ pot_status pot_render(const pot_tree *t, const pot_camera *cams, int32_t n_cams,
     p.H = H;
     p.tiles_x = (W + kTileW - 1) / kTileW;
     p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
+    if (p.tiles_per_cam * ((int64_t)n_cams + 16) >= (1ll << 32))
+        return tile_limit_error();
     p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
     const pot_camera *d_cams = reinterpret_cast<const pot_camera *>(sp + cam_off);
     const bool host_out = !is_device_ptr(rgb) || (t_final && !is_device_ptr(t_final));
@@ -696,6 +703,8 @@ pot_status pot_visibility(const pot_tree *t, const pot_camera *cams, int32_t n_c
     p.H = H;
     p.tiles_x = (W + kTileW - 1) / kTileW;
     p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
+    if (p.tiles_per_cam * ((int64_t)n_cams + 16) >= (1ll << 32))
+        return tile_limit_error();
     p.n_tiles = p.tiles_per_cam * n_cams;
     p.tile_counter = reinterpret_cast<unsigned long long *>(sp);
     POT_CUDA(launch_visibility(p, t, max_weight, s), "visibility");

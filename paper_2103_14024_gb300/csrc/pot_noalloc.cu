@@ -187,6 +187,8 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
     p.view_group = render_view_group(n_cams);
     p.tiles_x = (W + kTileW - 1) / kTileW;
     p.tiles_per_cam = (int64_t)p.tiles_x * ((H + kTileH - 1) / kTileH);
+    if (p.tiles_per_cam * ((int64_t)n_cams + 16) >= (1ll << 32))
+        return na_fail(POT_ERR_INVALID_ARG, "too many pixels in one call (tiles must stay below 2^32)");
     p.n_tiles = p.tiles_per_cam * n_cams;
     p.rgb = rgb;
     p.t_final = t_final;

@@ -304,14 +304,17 @@ __device__ __forceinline__ bool tile_ray(const RenderParams &p, unsigned long lo
         // tiles of a group of G consecutive cameras are interleaved: the same
         // tile of each camera of the group in turn, so neighbouring views
         // (which touch nearly the same leaves) share L1/L2
-        const int64_t G = p.view_group;
-        const int64_t group = (int64_t)tile / (p.tiles_per_cam * G);
-        const int64_t in_group = (int64_t)tile - group * p.tiles_per_cam * G;
-        const int64_t gsize = min(G, (int64_t)p.n_cams - group * G);
-        const int64_t cam = group * G + in_group % gsize;
-        const int64_t rem = in_group / gsize;
-        const int ty = (int)(rem / p.tiles_x);
-        const int tx = (int)(rem - (int64_t)ty * p.tiles_x);
+        // 32-bit arithmetic: the host keeps tile counts below 2^32
+        const uint32_t tl = (uint32_t)tile;
+        const uint32_t G = (uint32_t)p.view_group;
+        const uint32_t per_group = (uint32_t)p.tiles_per_cam * G;
+        const uint32_t group = tl / per_group;
+        const uint32_t in_group = tl - group * per_group;
+        const uint32_t gsize = min(G, (uint32_t)p.n_cams - group * G);
+        const int64_t cam = (int64_t)(group * G + in_group % gsize);
+        const uint32_t rem = in_group / gsize;
+        const int ty = (int)(rem / (uint32_t)p.tiles_x);
+        const int tx = (int)(rem - (uint32_t)ty * (uint32_t)p.tiles_x);
         const int i = tx * kTileW + (slot % kTileW);
         const int j = ty * kTileH + (slot / kTileW);
         if (i >= p.W || j >= p.H) return false;
