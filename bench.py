@@ -35,8 +35,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 1.5504 GB read + 0.1125 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "243fe1ea203629b4", "bytes_per_launch": 20.78e9},
+    # 16-view capture (one view group): 1.8316 GB read + 0.1232 GB written, x 12.5 = 200-view launch
+    "f32": {"sha": "13e54d1c0f3fe9f8", "bytes_per_launch": 24.435e9},
 }
 
 
@@ -144,16 +144,20 @@ def oracle_sample_rays(cams, views, every):
     return np.concatenate(ci), np.concatenate(px), np.concatenate(py)
 
 
-def run_oracle_timing(scene, cams, views, every, steps=1):
-    """Times the oracle (as it stands) on the bounded sample; returns (rays/s, rays, seconds, threads)."""
+def run_oracle_timing(scene, cams, views, every, steps=1, chunk_views=8):
+    """Times the oracle (as it stands) on the bounded sample, ``chunk_views`` views per call so
+    that host memory stays small; returns (rays/s, rays per step, seconds, threads)."""
     from oracle import oracle
     ot = oracle.build_sparse(scene)
-    ci, px, py = oracle_sample_rays(cams, views, every)
-    t0 = time.perf_counter()
+    n, dt = 0, 0.0
     for _ in range(steps):
-        oracle.render_pixels(ot, cams, ci, px, py, gamma=GAMMA)
-    dt = time.perf_counter() - t0
-    return ci.shape[0] * steps / dt, ci.shape[0], dt, oracle.num_threads()
+        for c in range(0, len(views), chunk_views):
+            ci, px, py = oracle_sample_rays(cams, views[c:c + chunk_views], every)
+            t0 = time.perf_counter()
+            oracle.render_pixels(ot, cams, ci, px, py, gamma=GAMMA)
+            dt += time.perf_counter() - t0
+            n += ci.shape[0]
+    return n / dt, n // steps, dt, oracle.num_threads()
 
 
 def reference_arm(args):
@@ -343,7 +347,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "cb16"])
-    ap.add_argument("--variants", default="f16,bf16,cb16", help="extra leaf dtypes to time ('' for none)")
+    ap.add_argument("--variants", default="f16,bf16,cb16,f32-descent",
+                    help="extra leaf dtypes to time ('' for none); '<dtype>-descent' = that tree without its "
+                         "cell index (cells located by descending the child array)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
@@ -387,13 +393,16 @@ def main():
     ccams = pot.make_cameras(cams)
     rays = len(cams) * W * H
 
-    def measure(dtype, e2e=False):
+    def measure(variant, e2e=False):
+        dtype, _, mode = variant.partition("-")
         if dtype == "cb16":     # median-cut SH codebooks (2^16 entries per basis) of the f32 tree
             t32 = pot.Tree.from_scene(scene, dtype="f32")
             tree = t32.quantize(16)
             t32.free()
         else:
             tree = pot.Tree.from_scene(scene, dtype=dtype)
+        if mode == "descent":
+            tree.set_cell_index(False)
         info = tree.info()
         rgb = torch.empty((len(cams), H, W, 3), dtype=torch.float32, device="cuda")
 
@@ -440,7 +449,8 @@ def main():
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": workload_config(scene, args.dtype, len(cams)),
+        "config": dict(workload_config(scene, args.dtype, len(cams)),
+                       cell_index_bytes=int(main_res["info"]["index_bytes"])),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"hbm_gbs of {peak_kind}",
@@ -471,7 +481,7 @@ def main():
     for vd in [v for v in args.variants.split(",") if v and v != args.dtype and extras]:
         r = measure(vd)
         w = r["wall"]
-        vb = algorithmic_bytes(pot, torch, r["tree"], cams, vd, int(r["info"]["leaf_bytes"]))
+        vb = algorithmic_bytes(pot, torch, r["tree"], cams, vd.partition("-")[0], int(r["info"]["leaf_bytes"]))
         avg = sum(r["per"]) / len(r["per"])
         variants[vd] = {"value": round(world * rays / (w / args.steps) / 1e6, 3),
                         "ms_per_step": round(1e3 * w / args.steps, 3),
@@ -480,7 +490,8 @@ def main():
                                      "frac": round(vb["hbm_bytes"] / (avg * 1e-3) / 1e9 / peak, 4),
                                      "traffic": (NCU_TRAFFIC.get(vd, {}).get("bytes_per_launch")
                                                  if NCU_TRAFFIC.get(vd, {}).get("sha") == sha else None)},
-                        "clocks": r["clk"], "leaf_bytes": int(r["info"]["leaf_bytes"])}
+                        "clocks": r["clk"], "leaf_bytes": int(r["info"]["leaf_bytes"]),
+                        "cell_index_bytes": int(r["info"]["index_bytes"])}
         r["tree"].free()
     if variants:
         line["variants"] = variants
@@ -489,10 +500,10 @@ def main():
     if not args.no_serve and extras:
         line["serve"] = serve_measure(pot, torch, synth, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        views = [0, 25, 50, 75, 100, 125, 150, 175]
+        views = list(range(0, N_VIEWS, 2))     # 100 of the 200 views, all pixels: ~10-20 s of CPU work
         rate, n, dt, thr = run_oracle_timing(scene, synth.cameras_main(N_VIEWS, W, H), views, 1)
         line["cpu_baseline"] = {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
-                                "sample": f"all pixels of views 0,25,...,175 of 200 ({n} rays, {dt:.1f} s on "
+                                "sample": f"all pixels of views 0,2,...,198 of 200 ({n} rays, {dt:.1f} s on "
                                           f"{thr} threads)"}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -121,6 +121,8 @@ typedef struct pot_tree_info {
     float bbox_size;
     int32_t saturated;    /* 1 if some value overflowed fp16/bf16 and was clamped */
     int32_t device;
+    int64_t index_bytes;  /* device bytes of the cell index (pot_tree_set_cell_index), 0 if none;
+                             included in bytes */
 } pot_tree_info;
 
 /* ---------------------------------------------------------------- build ---
@@ -157,6 +159,29 @@ pot_status pot_tree_set_values(pot_tree *tree, const float *sigma, const float *
 
 /* Synchronises the tree's device and frees it.  NULL is accepted. */
 pot_status pot_tree_free(pot_tree *tree);
+
+/* Cell index of a tree (the paper has no counterpart: an acceleration
+ * structure of this library).  A dense int32 array over the 2^D grid that
+ * gives, for every voxel, the leaf holding it (>= 0) or -(l + 1) for the empty
+ * node of level l that contains it -- exactly what the descent of the child
+ * array (Sec. 3.2 "Rendering") finds, so renders, gradients and visibility
+ * weights are bit-identical with and without it; with it, locating each cell
+ * is one 4-byte load instead of a descent.  Size 4 * 8^D bytes (537 MB at
+ * D = 9, 4.3 GB at D = 10); only for D <= 10.
+ *   Every tree of depth <= 10 that pot_build, pot_build_sparse,
+ *   pot_tree_prune or pot_tree_quantize creates gets one when the device has
+ *   room for it (pot_tree_info.index_bytes says whether it has).
+ *   enable = 1 builds it if absent (POT_ERR_UNSUPPORTED for D > 10,
+ *   POT_ERR_OOM when the device is full); enable = 0 synchronises the device
+ *   and frees it.  The tree's structure is never changed after creation, so
+ *   the index stays valid under pot_tree_set_values and pot_step.
+ *   Not thread-safe against renders of the same tree from other host threads. */
+pot_status pot_tree_set_cell_index(pot_tree *tree, int32_t enable, pot_stream stream);
+
+/* The cell index as a dense [R][R][R] int32 array indexed [x][y][z] (R = 2^D)
+ * into caller memory (host or device); POT_ERR_INVALID_ARG if the tree has
+ * none.  (No counterpart in the paper.) */
+pot_status pot_tree_export_cell_index(const pot_tree *tree, int32_t *out, pot_stream stream);
 
 /* ---------------------------------------------------------------- query ---
  * Leaf containing each point xyz [n][3] float32: leaf index >= 0, -1 for

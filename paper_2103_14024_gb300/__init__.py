@@ -67,7 +67,8 @@ class TreeInfo(C.Structure):
     _fields_ = [("depth", C.c_int32), ("sh_degree", C.c_int32), ("sh_dim", C.c_int32),
                 ("leaf_dtype", C.c_int32), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
                 ("bytes", C.c_int64), ("leaf_bytes", C.c_int64), ("bbox_lo", C.c_float * 3),
-                ("bbox_size", C.c_float), ("saturated", C.c_int32), ("device", C.c_int32)]
+                ("bbox_size", C.c_float), ("saturated", C.c_int32), ("device", C.c_int32),
+                ("index_bytes", C.c_int64)]
 
 
 assert C.sizeof(Camera) == 80
@@ -83,6 +84,8 @@ _SIGS = {
     "pot_tree_export": [_p, _p, _p, _p, _p, _p],
     "pot_tree_set_values": [_p, _p, _p, _p],
     "pot_tree_free": [_p],
+    "pot_tree_set_cell_index": [_p, C.c_int32, _p],
+    "pot_tree_export_cell_index": [_p, _p, _p],
     "pot_query": [_p, C.c_int64, _p, _p, _p],
     "pot_sh_basis": [C.c_int32, C.c_int64, _p, _p, _p],
     "pot_render": [_p, _p, C.c_int32, _p, _p, _p, _p],
@@ -271,6 +274,19 @@ class Tree:
         _check(lib().pot_tree_export(self.handle, _ptr(child), _ptr(sigma), _ptr(sh), _ptr(morton),
                                      _stream(stream)))
         return child, sigma, sh, morton
+
+    def set_cell_index(self, enable: bool = True, stream=None):
+        """``pot_tree_set_cell_index``: build (True) or free (False) the per-voxel cell index
+        that replaces the child-array descent when locating cells (depth <= 10)."""
+        _check(lib().pot_tree_set_cell_index(self.handle, 1 if enable else 0, _stream(stream)))
+
+    def export_cell_index(self, stream=None) -> np.ndarray:
+        """``pot_tree_export_cell_index``: int32 [R, R, R] indexed [x][y][z]: leaf index, or
+        -(l + 1) for a voxel inside an empty node of level l."""
+        R = 1 << self.info()["depth"]
+        out = np.zeros((R, R, R), np.int32)
+        _check(lib().pot_tree_export_cell_index(self.handle, _ptr(out), _stream(stream)))
+        return out
 
     def set_values(self, sigma, sh, stream=None):
         _check(lib().pot_tree_set_values(self.handle, _ptr(sigma), _ptr(sh), _stream(stream)))

@@ -203,7 +203,24 @@ void destroy_tree(pot_tree *t)
     cudaFree(t->sh);
     cudaFree(t->morton);
     cudaFree(t->codebook);
+    cudaFree(t->cells);
     delete t;
+}
+
+// Gives a new tree of depth <= kCellIndexMaxDepth its cell index.  A device
+// too full for it leaves the tree without one (cells are then found by
+// descending the child array); any other failure is returned.
+cudaError_t attach_cell_index(pot_tree *t, cudaStream_t s)
+{
+    if (t->desc.depth > kCellIndexMaxDepth) return cudaSuccess;
+    cudaError_t e = build_cell_index(t, s);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) t->bytes += cell_index_entries(t->desc.depth) * 4;
+    return e;
 }
 
 // Shared tail of both builds: codes, sigma, sh are device arrays of n kept voxels.
@@ -236,6 +253,11 @@ pot_status finish_build(const pot_build_desc *desc, int64_t n, const uint64_t *d
     t->saturated = (flags & 4u) ? 1 : 0;
     t->bytes = t->n_nodes * 32 + n * 8 + ((n * t->elem_bytes + 255) / 256) * 256 +
                n * (int64_t)t->stride * t->elem_bytes;
+    e = attach_cell_index(t, s);
+    if (e != cudaSuccess) {
+        destroy_tree(t);
+        return cuda_fail(e, "cell index");
+    }
     *out = t;
     return POT_OK;
 }
@@ -265,6 +287,7 @@ void fill_tree_params(RenderParams &p, const pot_tree *t, const pot_render_opts 
 {
     std::memset(&p, 0, sizeof(p));
     p.child = t->child;
+    p.cells = t->cells;
     p.sigma = t->sigma;
     p.sh = t->sh;
     p.codebook = t->codebook;
@@ -472,6 +495,7 @@ pot_status pot_tree_get_info(const pot_tree *t, pot_tree_info *info)
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = t->desc.bbox_lo[a];
     info->bbox_size = t->desc.bbox_size;
     info->saturated = t->saturated;
+    info->index_bytes = t->cells ? cell_index_entries(t->desc.depth) * 4 : 0;
     info->device = t->device;
     return POT_OK;
 }
@@ -526,6 +550,52 @@ pot_status pot_tree_set_values(pot_tree *t, const float *sigma, const float *sh,
 pot_status pot_tree_free(pot_tree *t)
 {
     destroy_tree(t);
+    return POT_OK;
+}
+
+pot_status pot_tree_export_cell_index(const pot_tree *t, int32_t *out, pot_stream stream)
+{
+    if (!t || !out) return fail(POT_ERR_INVALID_ARG, "NULL tree or out");
+    if (!t->cells) return fail(POT_ERR_INVALID_ARG, "tree has no cell index");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Out oo;
+    void *dout;
+    POT_CUDA(oo.bind(out, sizeof(int32_t) * ((size_t)1 << (3 * t->desc.depth)), s, &dout), "bind out");
+    POT_CUDA(export_cell_index(t, static_cast<int32_t *>(dout), s), "export cell index");
+    POT_CUDA(oo.finish(s), "copy out");
+    if (oo.host) POT_CUDA(cudaStreamSynchronize(s), "sync");
+    return POT_OK;
+}
+
+pot_status pot_tree_set_cell_index(pot_tree *t, int32_t enable, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (enable != 0 && enable != 1) return fail(POT_ERR_INVALID_ARG, "enable must be 0 or 1");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t bytes = cell_index_entries(t->desc.depth) * 4;
+    if (!enable) {
+        if (t->cells) {
+            POT_CUDA(cudaDeviceSynchronize(), "sync");
+            POT_CUDA(cudaFree(t->cells), "free cell index");
+            t->cells = nullptr;
+            t->bytes -= bytes;
+        }
+        return POT_OK;
+    }
+    if (t->cells) return POT_OK;
+    if (t->desc.depth > kCellIndexMaxDepth)
+        return fail(POT_ERR_UNSUPPORTED, "no cell index for depth %d (at most %d)", t->desc.depth,
+                    kCellIndexMaxDepth);
+    cudaError_t e = build_cell_index(t, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return fail(POT_ERR_OOM, "cell index: %lld bytes", (long long)bytes);
+    }
+    POT_CUDA(e, "cell index");
+    t->bytes += bytes;
     return POT_OK;
 }
 
@@ -756,6 +826,7 @@ pot_status pot_tree_quantize(const pot_tree *t, int32_t bits, pot_tree **out, po
     q->sh = nullptr;
     q->morton = nullptr;
     q->codebook = nullptr;
+    q->cells = nullptr;
     cudaError_t e = cudaMalloc(&q->child, sizeof(int32_t) * 8 * t->n_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&q->morton, sizeof(uint64_t) * (t->n_leaves > 0 ? t->n_leaves : 1));
     if (e == cudaSuccess)
@@ -770,6 +841,11 @@ pot_status pot_tree_quantize(const pot_tree *t, int32_t bits, pot_tree **out, po
     const int64_t n = t->n_leaves;
     q->bytes = q->n_nodes * 32 + n * 8 + ((n * 2 + 255) / 256) * 256 + n * (int64_t)q->stride * 2 +
                (int64_t)t->K * 65536 * 8;
+    e = attach_cell_index(q, s);
+    if (e != cudaSuccess) {
+        destroy_tree(q);
+        return cuda_fail(e, "cell index");
+    }
     *out = q;
     return POT_OK;
 }

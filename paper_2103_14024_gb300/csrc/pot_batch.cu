@@ -17,6 +17,7 @@ namespace {
 
 struct BatchItem {
     const int32_t *child;
+    const int32_t *cells;
     const void *sigma;
     const void *sh;
     const void *codebook;
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
         if (i < it.W && j < it.H) {
             RenderParams p;
             p.child = it.child;
+            p.cells = it.cells;
             p.depth = it.depth;
             p.R = it.R;
             p.lo[0] = it.lo[0];
@@ -141,6 +143,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         const pot_tree *t = r.tree;
         BatchItem &b = desc[k];
         b.child = t->child;
+        b.cells = t->cells;
         b.sigma = t->sigma;
         b.sh = t->sh;
         b.codebook = t->codebook;

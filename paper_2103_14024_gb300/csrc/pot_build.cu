@@ -300,7 +300,84 @@ __global__ void k_dense_gather(int depth, int K, const float *sigma, const float
     }
 }
 
+// Cell index entry of every voxel: a root descent of the child array (the
+// query's rule), written in the index's brick order so that stores coalesce.
+__global__ void k_cell_index(int D, const int32_t *child, int32_t *cells)
+{
+    const int nb = D > 2 ? D - 2 : 0;
+    const uint32_t R = 1u << D, bmask = (1u << nb) - 1u;
+    const int64_t n = cell_index_entries(D);
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t in = (uint32_t)o & 63u, brick = (uint32_t)(o >> 6);
+        const uint32_t x = ((brick >> (2 * nb)) << 2) | (in >> 4);
+        const uint32_t y = (((brick >> nb) & bmask) << 2) | ((in >> 2) & 3u);
+        const uint32_t z = ((brick & bmask) << 2) | (in & 3u);
+        int32_t v = -1;  // entries of voxels outside a grid smaller than one brick are never read
+        if (x < R && y < R && z < R) {
+            int32_t node = 0;
+            for (int l = 0; l < D; ++l) {
+                const int b = D - 1 - l;
+                const int slot = (int)((((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u));
+                const int32_t c = child[(int64_t)node * 8 + slot];
+                if (c > 0 && l < D - 1) {
+                    node = c;
+                    continue;
+                }
+                v = c < 0 ? -c - 1 : -(l + 2);  // an empty slot of a level-l node is a level-(l+1) cell
+                break;
+            }
+        }
+        cells[o] = v;
+    }
+}
+
+// Index entries in x-major voxel order (export).
+__global__ void k_cell_index_export(int D, const int32_t *cells, int32_t *out)
+{
+    const int64_t n = 1ll << (3 * D);
+    const uint32_t m = (1u << D) - 1u;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
+        out[v] = cells[cell_index_offset(x, y, z, D)];
+    }
+}
+
 }  // namespace
+
+cudaError_t export_cell_index(const pot_tree *t, int32_t *out, cudaStream_t s)
+{
+    const int D = t->desc.depth;
+    const int64_t n = 1ll << (3 * D);
+    const int64_t want = (n + 255) / 256;
+    k_cell_index_export<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(D, t->cells, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t build_cell_index(pot_tree *t, cudaStream_t s)
+{
+    const int D = t->desc.depth;
+    if (D > kCellIndexMaxDepth) return cudaErrorNotSupported;
+    const int64_t n = cell_index_entries(D);
+    int32_t *cells = nullptr;
+    cudaError_t e = cudaMalloc(&cells, sizeof(int32_t) * n);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) {
+        const int64_t want = (n + 255) / 256, cap = (int64_t)sms * 16;
+        k_cell_index<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(D, t->child, cells);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        cudaFree(cells);
+        return e;
+    }
+    t->cells = cells;
+    return cudaSuccess;
+}
 
 cudaError_t scan_inclusive(const int *in, int *out, int64_t n, cudaStream_t s);
 

@@ -20,6 +20,30 @@ namespace pot {
 constexpr int kMaxDepth = 12;
 
 // ------------------------------------------------------------------------
+// cell index: for every voxel of the 2^D grid, the leaf that holds it (>= 0)
+// or -(level + 1) of the empty node that contains it, where an empty node of
+// level l spans 2^(D-l) voxels per axis.  Locating a cell (the octree descent
+// of Sec. 3.2 "Rendering") becomes one 4-byte load.  Entries are stored in
+// 4x4x4 bricks (bricks ordered x, y, z; inside a brick x, y, z), so that a
+// 128-byte line covers 2x4x4 voxels and neighbouring rays share lines.
+// ------------------------------------------------------------------------
+constexpr int kCellIndexMaxDepth = 10;  // 4 * 8^10 bytes = 4.3 GB
+
+__host__ __device__ __forceinline__ uint32_t cell_index_offset(uint32_t x, uint32_t y, uint32_t z, int D)
+{
+    const int nb = D > 2 ? D - 2 : 0;  // log2 of bricks per axis
+    const uint32_t brick = ((x >> 2) << (2 * nb)) | ((y >> 2) << nb) | (z >> 2);
+    return (brick << 6) | ((x & 3u) << 4) | ((y & 3u) << 2) | (z & 3u);
+}
+
+// Entries of the index of a depth-D tree (at least one brick).
+__host__ __device__ __forceinline__ int64_t cell_index_entries(int D)
+{
+    const int64_t n = 1ll << (3 * D);
+    return n < 64 ? 64 : n;
+}
+
+// ------------------------------------------------------------------------
 // error-free transformations
 // ------------------------------------------------------------------------
 struct df {

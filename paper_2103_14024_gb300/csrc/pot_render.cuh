@@ -5,8 +5,10 @@
 // until none is left (persistent grid, one wave of resident blocks).  Per ray:
 //   a1 pinhole ray (fp32 expression of the public header)
 //   a2 clip to the tree box and to [near, far]
-//   a3 locate the cell: descend the child array from the deepest ancestor the
-//      new voxel shares with the previous one (ancestor stack in shared memory)
+//   a3 locate the cell: one load from the tree's cell index (leaf, or level of
+//      the empty node, per voxel), or, for trees without one, a descent of the
+//      child array from the deepest ancestor the new voxel shares with the
+//      previous one (ancestor stack in shared memory)
 //   a4 exit time of the cell (double-float plane crossings); an empty node of
 //      any size is crossed in one step (Sec. 3.2 "Rendering")
 //   a5 leaf fetch: sigma and the SH record in 16-byte vector loads
@@ -61,12 +63,19 @@ struct Walker {
     int kx[3];
     df tcx[3];
 
-    // a3: descend to the cell of voxel nq from the deepest ancestor it shares
-    // with voxel pq (whose path the stack holds up to lvl_valid)
+    // a3: the cell of voxel nq: one load from the cell index when the tree
+    // has one, else a descent from the deepest ancestor nq shares with voxel
+    // pq (whose path the stack holds up to lvl_valid)
     __device__ __forceinline__ void descend(const RenderParams &p, int32_t *stk, const int nq[3], const int pq[3],
                                             int &out_leaf, int &out_lvl)
     {
         const int D = p.depth;
+        if (p.cells) {
+            const int v = __ldg(p.cells + cell_index_offset((uint32_t)nq[0], (uint32_t)nq[1], (uint32_t)nq[2], D));
+            out_leaf = v >= 0 ? v : -1;
+            out_lvl = v >= 0 ? D : -v - 1;
+            return;
+        }
         const unsigned diff = (unsigned)((nq[0] ^ pq[0]) | (nq[1] ^ pq[1]) | (nq[2] ^ pq[2]));
         const int lc = diff ? D - 32 + __clz(diff) : D - 1;  // level of the common ancestor
         int l = min(lc, lvl_valid);

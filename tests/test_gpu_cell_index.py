@@ -1,0 +1,179 @@
+"""Cell index (per-voxel leaf / empty-node level, the library's replacement for
+the child-array descent when locating cells): its entries against their
+definition from the occupied voxels alone, and renders, counts, gradients,
+visibility weights and batched renders bit-identical with and without it."""
+import numpy as np
+import pytest
+
+from paper_2103_14024_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pot():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2103_14024_gb300 as P
+    P.lib()
+    return P
+
+
+def _expected_index(sc):
+    """Entry of every voxel [x][y][z] from the occupied Morton codes: the leaf
+    rank, else -(l + 1) for the coarsest level l whose block around the voxel
+    holds no occupied voxel (the empty child of an existing node)."""
+    D, R = sc.depth, 1 << sc.depth
+    g = np.arange(R, dtype=np.uint64)
+    x, y, z = np.meshgrid(g, g, g, indexing="ij")
+    m = S.morton_encode(x.ravel(), y.ravel(), z.ravel(), D).astype(np.uint64)
+    occ = np.sort(sc.morton.astype(np.uint64))
+    out = np.zeros(m.shape, np.int64)
+    level = np.full(m.shape, -1, np.int64)
+    for l in range(1, D + 1):
+        sh = np.uint64(3 * (D - l))
+        inside = np.isin(m >> sh, np.unique(occ >> sh))
+        level[(level < 0) & ~inside] = l
+    empty = level > 0
+    out[empty] = -(level[empty] + 1)
+    out[~empty] = np.searchsorted(occ, m[~empty])
+    return out.reshape(R, R, R).astype(np.int32)
+
+
+@pytest.mark.parametrize("seed,D,p_occ", [(81, 1, 0.5), (82, 2, 0.3), (83, 3, 0.2), (84, 4, 0.05),
+                                          (85, 5, 0.3), (86, 6, 0.02), (87, 7, 0.01)])
+def test_index_entries_match_definition(pot, seed, D, p_occ):
+    sc = S.scene_random(seed, D, 1, p_occ=p_occ)
+    t = pot.Tree.from_scene(sc)
+    info = t.info()
+    assert info["index_bytes"] == 4 * max(64, 8 ** D)
+    assert np.array_equal(t.export_cell_index(), _expected_index(sc))
+
+
+def test_index_empty_and_single_leaf_trees(pot):
+    sc = S.scene_random(88, 4, 0, p_occ=0.3)
+    for n in (0, 1):
+        s = sc.replace(morton=sc.morton[:n], sigma=sc.sigma[:n], sh=sc.sh[:n])
+        t = pot.Tree.from_scene(s)
+        assert np.array_equal(t.export_cell_index(), _expected_index(s))
+
+
+def test_index_toggle_and_limits(pot):
+    sc = S.scene_random(89, 5, 2, p_occ=0.3)
+    t = pot.Tree.from_scene(sc)
+    full = t.info()
+    t.set_cell_index(False)
+    t.set_cell_index(False)                       # idempotent
+    off = t.info()
+    assert off["index_bytes"] == 0 and off["bytes"] == full["bytes"] - full["index_bytes"]
+    with pytest.raises(pot.PotError) as e:
+        t.export_cell_index()
+    assert e.value.status == pot.POT_ERR_INVALID_ARG
+    t.set_cell_index(True)
+    assert t.info() == full
+    # depth 11: no index (4 * 8^11 bytes), cells found by the descent
+    m = S.morton_encode(np.array([5, 1000, 2047], np.uint64), np.array([7, 3, 2047], np.uint64),
+                        np.array([9, 1500, 0], np.uint64), 11)
+    order = np.argsort(m)
+    deep = S.Scene(depth=11, bbox_lo=(-1.0, -1.0, -1.0), bbox_size=2.0, sh_degree=0,
+                   morton=m[order].astype(np.uint64), sigma=np.float32([5.0, 6.0, 7.0]),
+                   sh=np.zeros((3, 1, 3), np.float32))
+    td = pot.Tree.from_scene(deep)
+    assert td.info()["index_bytes"] == 0
+    with pytest.raises(pot.PotError) as e:
+        td.set_cell_index(True)
+    assert e.value.status == pot.POT_ERR_UNSUPPORTED
+
+
+def _both(pot, t, fn):
+    """fn(tree) with the cell index, then without it (restored afterwards)."""
+    a = fn(t)
+    t.set_cell_index(False)
+    try:
+        b = fn(t)
+    finally:
+        t.set_cell_index(True)
+    return a, b
+
+
+def _edge_rays(sc):
+    h = np.float32(sc.bbox_size / sc.res)
+    lo = np.float32(sc.bbox_lo[0])
+    o, d = [], []
+    for k in range(0, sc.res + 1, max(1, sc.res // 8)):
+        a = lo + np.float32(k) * h
+        o += [(a, a, 3.0), (a, 3.0, a), (-3.0, a, a), (a, -3.0, -3.0)]
+        d += [(0, 0, -1), (0, -1, 0), (1, 0, 0), (0, 1, 1)]
+    return np.array(o, np.float32), np.array(d, np.float32)
+
+
+@pytest.mark.parametrize("seed,D,deg,dtype", [(91, 2, 0, "f32"), (92, 4, 1, "f16"), (93, 5, 3, "f32"),
+                                              (94, 6, 2, "bf16"), (95, 7, 3, "f32"), (96, 8, 1, "f16")])
+@pytest.mark.parametrize("gamma", [0.0, 1e-3])
+def test_renders_bit_identical(pot, seed, D, deg, dtype, gamma):
+    import torch
+    sc = S.scene_random(seed, D, deg, p_occ=0.3, sigma_mu=2.0)
+    t = pot.Tree.from_scene(sc, dtype=dtype)
+    o, d = S.random_rays(seed, 20000, radius=3.0, spread=1.0)
+    eo, ed = _edge_rays(sc)
+    o = torch.from_numpy(np.concatenate([o, eo])).cuda()
+    d = torch.from_numpy(np.concatenate([d, ed])).cuda()
+    cams = S.make_cameras(S.orbit_c2ws(5, radius=3.0, elevation_deg=25.0), 61, 47, 50.0)
+    n = o.shape[0]
+
+    def run(tree):
+        seg = torch.zeros(n, dtype=torch.int32, device="cuda")
+        touched = torch.zeros(max(1, sc.n), dtype=torch.uint8, device="cuda")
+        rgb, tf = pot.render_rays(tree, o, d, near=0.3, far=8.0, bg=(0.1, 0.2, 0.3), gamma=gamma,
+                                  want_t_final=True, seg_count=seg, leaf_touched=touched)
+        img, itf = pot.render(tree, cams, gamma=gamma, bg=(0.5, 0.5, 0.5), want_t_final=True)
+        return rgb, tf, seg, touched, img, itf
+
+    a, b = _both(pot, t, run)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    pot.check()
+
+
+def test_backward_and_visibility_bit_identical(pot):
+    import torch
+    sc = S.scene_random(97, 6, 3, p_occ=0.3, sigma_mu=2.0)
+    t = pot.Tree.from_scene(sc)
+    o, d = S.random_rays(97, 30000, radius=3.0, spread=1.0)
+    o, d = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    g = torch.from_numpy(S.uniform(97, 5, np.arange(3 * o.shape[0], dtype=np.uint64)).astype(np.float32)
+                         .reshape(-1, 3) - 0.5).cuda()
+    cams = S.make_cameras(S.orbit_c2ws(4, radius=3.0), 48, 40, 40.0)
+
+    def run(tree):
+        rgb = pot.render_rays(tree, o, d, gamma=1e-3)
+        gs, gsh = pot.render_backward(tree, o, d, g, rgb_fwd=rgb, gamma=1e-3)
+        w = pot.visibility(tree, cams, gamma=1e-3)
+        return gs, gsh, w
+
+    a, b = _both(pot, t, run)
+    # gradients are sums of float reductions whose order varies from run to
+    # run; the maxima of the visibility weights do not depend on the order
+    for x, y in zip(a[:2], b[:2]):
+        assert torch.allclose(x, y, rtol=1e-5, atol=1e-6)
+    assert torch.equal(a[2], b[2])
+    pot.check()
+
+
+def test_batch_mixes_trees_with_and_without_index(pot):
+    import torch
+    trees = [pot.Tree.from_scene(S.scene_random(98 + i, 5 + i, 2, p_occ=0.3), dtype="f16") for i in range(3)]
+    trees[1].set_cell_index(False)
+    cams = [S.make_cameras([S.look_at((4 * np.cos(a), 4 * np.sin(a), 1.5))], 40 + 7 * i, 30 + 5 * i, 40.0,
+                           near=1.0, far=8.0)[0] for i, a in enumerate(np.linspace(0, 5, 6))]
+    outs = [torch.full((int(c["height"]), int(c["width"]), 3), -1.0, device="cuda") for c in cams]
+    items = [(trees[i % 3], c, out, (0.0, 0.0, 0.0), 1e-3, None) for i, (c, out) in enumerate(zip(cams, outs))]
+    pot.render_batch(items)
+    for i, (c, out) in enumerate(zip(cams, outs)):
+        tr = trees[i % 3]
+        alone = pot.render(tr, c[None], gamma=1e-3)[0]
+        assert torch.equal(out, alone)
+        tr.set_cell_index(False)
+        assert torch.equal(out, pot.render(tr, c[None], gamma=1e-3)[0])
+        tr.set_cell_index(tr is not trees[1])
+    pot.check()
