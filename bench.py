@@ -35,8 +35,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 1.8316 GB read + 0.1232 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "13e54d1c0f3fe9f8", "bytes_per_launch": 24.435e9},
+    # 16-view capture (one view group): 1.8443 GB read + 0.1231 GB written, x 12.5 = 200-view launch
+    "f32": {"sha": "8b1dc2e6b1829b4c", "bytes_per_launch": 24.592e9},
 }
 
 

@@ -69,7 +69,9 @@ __device__ __forceinline__ float df_sub(df a, df b)
     return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
 }
 
-__device__ __forceinline__ bool df_lt(df a, df b) { return df_sub(a, b) < 0.f; }
+// a < b, decided as (a.hi - b.hi) + (a.lo - b.lo) < 0 would be (the sign of a
+// rounded sum is the sign of the exact sum), with one addition fewer.
+__device__ __forceinline__ bool df_lt(df a, df b) { return __fsub_rn(a.hi, b.hi) < __fsub_rn(b.lo, a.lo); }
 
 // Time t at which o + t d crosses plane k of one axis, i.e.
 // (lo + k h - o) / d, with A = lo - o given exactly as Ahi + Alo and rd = 1/d.
@@ -291,32 +293,71 @@ __host__ __device__ constexpr int sh_stride(int K)
 // codebook leaves: K codes (uint16) per record
 __host__ __device__ constexpr int cb_stride(int K) { return (K + 7) / 8 * 8; }
 
-// x_c = sum_k sh[k][c] Y_k for the three channels of one leaf; the record is
-// read in chunks of up to four 16-byte loads to bound live registers (the
-// lines were prefetched into L1 a step earlier).
-// The per-ray SH basis, either in registers (a plain array) or in shared
-// memory with one column per thread (stride = threads per block).
-template <int STRIDE>
+#ifndef POT_LDG256
+// read SH records with 32-byte loads where a record is a whole number of 32-byte
+// units (K = 16 in every type; K = 9 and 4 in fp16 / bf16): half the load
+// instructions, and fewer L1 wavefronts for the divergent gathers
+#define POT_LDG256 1
+#endif
+
+// One 32-byte read-only load (sm_100 and later; p 32-byte aligned).
+__device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b)
+{
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+        : "l"(p));
+}
+
+// The per-ray SH basis in shared memory: this thread's column of a block-wide
+// [K][THREADS] float array (consecutive threads hit consecutive banks).
+// (Rows of float4 read with 16-byte loads measured slower: with the 32-byte
+// record loads they push the render kernel past 64 registers.)
+template <int K, int THREADS>
 struct SmemY {
     const float *base;
-    __device__ __forceinline__ float operator[](int k) const { return base[k * STRIDE]; }
+    __device__ __forceinline__ float operator[](int k) const { return base[k * THREADS]; }
+    // yv[k] = Y_k for k0 <= k <= k1 (constant bounds once unrolled)
+    __device__ __forceinline__ void fetch(float *yv, int k0, int k1) const
+    {
+#pragma unroll
+        for (int k = k0; k <= k1; ++k) yv[k] = base[k * THREADS];
+    }
+    __device__ __forceinline__ static void store(float *col, const float *Yt)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) col[k * THREADS] = Yt[k];
+    }
 };
 
+// x_c = sum_k sh[k][c] Y_k for the three channels of one leaf.  The record
+// is read in chunks of 64 bytes (two 32-byte or four 16-byte loads) to bound
+// live registers; each chunk fetches the basis values it multiplies.
 template <int K, typename T, typename YT>
 __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const YT &Y, float *x, const void *)
 {
     constexpr int V = Store<T>::kVec;
     constexpr int N = 3 * K;
-    constexpr int NV = (N + V - 1) / V;
-    constexpr int CH = 4;
+    constexpr int NV = (N + V - 1) / V;  // 16-byte units per record
+    constexpr bool WIDE = POT_LDG256 && NV % 2 == 0;
+    constexpr int CH = 4;                // 16-byte units per chunk
     const uint4 *p = reinterpret_cast<const uint4 *>(sh + leaf * (int64_t)(NV * V));
     x[0] = x[1] = x[2] = 0.f;
 #pragma unroll
     for (int v0 = 0; v0 < NV; v0 += CH) {
         uint4 raw[CH];
 #pragma unroll
-        for (int j = 0; j < CH; ++j)
-            if (v0 + j < NV) raw[j] = __ldg(p + v0 + j);
+        for (int j = 0; j < CH; ++j) {
+            if (v0 + j < NV) {
+                if (WIDE) {
+                    if (j % 2 == 0) ldg256(p + v0 + j, raw[j], raw[j + 1]);
+                } else {
+                    raw[j] = __ldg(p + v0 + j);
+                }
+            }
+        }
+        const int e_hi = min((v0 + CH) * V, N) - 1;
+        float yv[K];
+        Y.fetch(yv, v0 * V / 3, e_hi / 3);
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             if (v0 + j < NV) {
@@ -325,7 +366,7 @@ __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const YT 
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const int idx = (v0 + j) * V + e;
-                    if (idx < N) x[idx % 3] = fmaf(f[e], Y[idx / 3], x[idx % 3]);
+                    if (idx < N) x[idx % 3] = fmaf(f[e], yv[idx / 3], x[idx % 3]);
                 }
             }
         }
@@ -341,7 +382,7 @@ __device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, con
     const uint2 *book = static_cast<const uint2 *>(cb);
     uint4 raw[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) raw[v] = __ldg(p + v);
+    for (int v = 0; v < NV; ++v) raw[v] = __ldg(p + v);  // (one 32-byte load here measured 11 % slower)
     uint2 e[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {

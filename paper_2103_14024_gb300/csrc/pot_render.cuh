@@ -27,11 +27,6 @@ constexpr int kBlock = 256;
 #ifndef POT_RENDER_MIN_BLOCKS
 #define POT_RENDER_MIN_BLOCKS 4  // resident blocks per SM the register budget is cut for (64 registers)
 #endif
-#ifndef POT_Y_SMEM
-// keep the per-ray SH basis in shared memory instead of registers: frees 16
-// registers per thread, which lets 4 blocks (32 warps) reside per SM
-#define POT_Y_SMEM 1
-#endif
 #ifndef POT_PREFETCH
 // prefetch the next cell's leaf into L1 before shading the current one (helped
 // while leaves streamed from DRAM; with neighbouring views sharing L2 it costs
@@ -50,13 +45,10 @@ template <int K, typename T>
 struct Walker {
     float d[3], rd[3], Ahi[3], Alo[3], margin[3];
     float len;
-#if POT_Y_SMEM
-    float *ysm;  // this thread's column of the block's [K][kBlock] shared array
-    __device__ __forceinline__ SmemY<kBlock> Y() const { return {ysm}; }
-#else
-    float Yr[K];
-    __device__ __forceinline__ const float *Y() const { return Yr; }
-#endif
+    // the per-ray SH basis lives in shared memory (this thread's part of the
+    // block's array), not in 16 registers: that lets 4 blocks (32 warps) reside per SM
+    float *ysm;
+    __device__ __forceinline__ SmemY<K, kBlock> Y() const { return {ysm}; }
     df t, tout;
     int q[3];
     int leaf, cell_lvl, lvl_valid, step_i;
@@ -108,16 +100,11 @@ struct Walker {
         len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
         if (!(len > 0.f) || !(len < 3.0e38f)) return false;
         const float invlen = __frcp_rn(len);
-#if POT_Y_SMEM
         {
             float Yt[K];
             sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Yt);
-#pragma unroll
-            for (int k = 0; k < K; ++k) ysm[k * kBlock] = Yt[k];
+            SmemY<K, kBlock>::store(ysm, Yt);
         }
-#else
-        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Yr);
-#endif
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
@@ -245,11 +232,11 @@ struct Walker {
     }
 };
 
-// Per-thread scratch of a walk in shared memory: the ancestor stack and (with
-// POT_Y_SMEM) the SH basis.  Declared once per kernel.
+// Per-thread scratch of a walk in shared memory: the ancestor stack and the
+// SH basis (SmemY).  Declared once per kernel.
 #define POT_WALK_SHARED(K)                                          \
     __shared__ int32_t stk_sh[kMaxDepth][kBlock];                   \
-    __shared__ float ysm_sh[POT_Y_SMEM ? (K) : 1][kBlock];          \
+    __shared__ float ysm_sh[(K)][kBlock];                           \
     int32_t *stk = &stk_sh[0][threadIdx.x];                         \
     float *ysm = &ysm_sh[0][threadIdx.x];                           \
     (void)ysm;
@@ -261,11 +248,7 @@ __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr
                                          float near, float far, Visitor &vis)
 {
     Walker<K, T> w;
-#if POT_Y_SMEM
     w.ysm = ysm;
-#else
-    (void)ysm;
-#endif
     if (!w.begin(p, stk, sig_arr, sh_arr, o, d, near, far)) return;
     while (w.step(p, stk, sig_arr, sh_arr, vis)) {
     }
