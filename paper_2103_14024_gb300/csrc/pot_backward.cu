@@ -151,16 +151,11 @@ cudaError_t launch_backward_t(const BackwardParams &bp, int K, bool have_fwd, cu
     POT_PICK(16)
 #undef POT_PICK
     if (!fn) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    const size_t smem = walk_smem_bytes(bp.r.cells == nullptr);
+    unsigned grid = 0;
+    cudaError_t e = persistent_grid(fn, smem, bp.r.n_tiles, 0, &grid);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (bp.r.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    fn<<<(unsigned)blocks, kBlock, 0, s>>>(bp);
+    fn<<<grid, kBlock, smem, s>>>(bp);
     count_launch();
     return cudaGetLastError();
 }

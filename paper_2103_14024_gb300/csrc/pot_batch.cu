@@ -101,22 +101,17 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
 }
 
 template <typename T>
-cudaError_t launch_batch_t(const BatchParams &bp, int K, cudaStream_t s)
+cudaError_t launch_batch_t(const BatchParams &bp, int K, bool need_stack, cudaStream_t s)
 {
     using Fn = void (*)(const BatchParams);
     Fn fn = K == 1 ? batch_kernel<1, T> : K == 4 ? batch_kernel<4, T> : K == 9 ? batch_kernel<9, T>
           : K == 16 ? batch_kernel<16, T> : nullptr;
     if (!fn) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    const size_t smem = walk_smem_bytes(need_stack);
+    unsigned grid = 0;
+    cudaError_t e = persistent_grid(fn, smem, bp.n_tiles, 0, &grid);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (bp.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    fn<<<(unsigned)blocks, kBlock, 0, s>>>(bp);
+    fn<<<grid, kBlock, smem, s>>>(bp);
     count_launch();
     return cudaGetLastError();
 }
@@ -185,11 +180,13 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         bp.tile_counter = reinterpret_cast<unsigned long long *>(cb) + g;
         bp.err = err;
         const pot_tree *t = items[order[a]].tree;
+        bool need_stack = false;  // some tree of the group without a cell index
+        for (int k = a; k < b; ++k) need_stack = need_stack || desc[k].cells == nullptr;
         switch (t->desc.leaf_dtype) {
-        case POT_F32: e = launch_batch_t<float>(bp, t->K, s); break;
-        case POT_F16: e = launch_batch_t<__half>(bp, t->K, s); break;
-        case POT_CB16: e = launch_batch_t<cb16>(bp, t->K, s); break;
-        default: e = launch_batch_t<__nv_bfloat16>(bp, t->K, s); break;
+        case POT_F32: e = launch_batch_t<float>(bp, t->K, need_stack, s); break;
+        case POT_F16: e = launch_batch_t<__half>(bp, t->K, need_stack, s); break;
+        case POT_CB16: e = launch_batch_t<cb16>(bp, t->K, need_stack, s); break;
+        default: e = launch_batch_t<__nv_bfloat16>(bp, t->K, need_stack, s); break;
         }
     }
     cudaFreeAsync(buf, s);

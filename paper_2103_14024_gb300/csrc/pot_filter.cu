@@ -56,16 +56,11 @@ cudaError_t launch_visibility_t(const RenderParams &p, int K, float *max_w, cuda
     Fn fn = K == 1 ? visibility_kernel<1, T> : K == 4 ? visibility_kernel<4, T> : K == 9 ? visibility_kernel<9, T>
           : K == 16 ? visibility_kernel<16, T> : nullptr;
     if (!fn) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    const size_t smem = walk_smem_bytes(p.cells == nullptr);
+    unsigned grid = 0;
+    cudaError_t e = persistent_grid(fn, smem, p.n_tiles, 0, &grid);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (p.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    fn<<<(unsigned)blocks, kBlock, 0, s>>>(p, max_w);
+    fn<<<grid, kBlock, smem, s>>>(p, max_w);
     count_launch();
     return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ struct Walker {
             q[a] = min(max(v, 0), R - 1);
         }
         lvl_valid = 0;
-        stk[0] = 0;
+        if (!p.cells) stk[0] = 0;  // the stack exists only for trees without a cell index
         descend(p, stk, q, q, leaf, cell_lvl);
         if (POT_PREFETCH && leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
         // exit plane (voxel index) and crossing time per axis, recomputed only
@@ -232,14 +232,40 @@ struct Walker {
     }
 };
 
-// Per-thread scratch of a walk in shared memory: the ancestor stack and the
-// SH basis (SmemY).  Declared once per kernel.
+// Per-thread scratch of a walk in shared memory: the SH basis (SmemY) and
+// the ancestor stack [kMaxDepth][kBlock] in dynamic shared memory, which a
+// launch provides (walk_smem_bytes) only when some tree of it has no cell
+// index; without it the space goes to L1.  Declared once per kernel.
 #define POT_WALK_SHARED(K)                                          \
-    __shared__ int32_t stk_sh[kMaxDepth][kBlock];                   \
+    extern __shared__ int32_t walk_stack_sh[];                      \
     __shared__ float ysm_sh[(K)][kBlock];                           \
-    int32_t *stk = &stk_sh[0][threadIdx.x];                         \
+    int32_t *stk = walk_stack_sh + threadIdx.x;                     \
     float *ysm = &ysm_sh[0][threadIdx.x];                           \
     (void)ysm;
+
+inline size_t walk_smem_bytes(bool need_stack)
+{
+    return need_stack ? sizeof(int32_t) * kMaxDepth * kBlock : 0;
+}
+
+// Grid of a persistent walk kernel: one wave of resident blocks (SMs x blocks
+// per SM for this kernel and shared memory), no more blocks than tiles need.
+template <typename Fn>
+cudaError_t persistent_grid(Fn fn, size_t smem, int64_t n_tiles, int max_blocks, unsigned *grid)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
+    if (blocks > need) blocks = need;
+    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    *grid = (unsigned)blocks;
+    return cudaSuccess;
+}
 
 // The whole walk of one ray.
 template <int K, typename T, typename Visitor>
@@ -386,17 +412,11 @@ cudaError_t launch_render_t(const RenderParams &p, int K, bool cams, bool count,
     POT_PICK(16)
 #undef POT_PICK
     if (!fn) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    const size_t smem = walk_smem_bytes(p.cells == nullptr);
+    unsigned grid = 0;
+    cudaError_t e = persistent_grid(fn, smem, p.n_tiles, max_blocks, &grid);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (p.n_tiles + (kBlock / 32) - 1) / (kBlock / 32);
-    if (blocks > need) blocks = need;
-    if (max_blocks > 0 && blocks > max_blocks) blocks = max_blocks;
-    if (blocks < 1) blocks = 1;
-    fn<<<(unsigned)blocks, kBlock, 0, s>>>(p);
+    fn<<<grid, kBlock, smem, s>>>(p);
     count_launch();
     return cudaGetLastError();
 }

@@ -58,7 +58,7 @@ def test_index_empty_and_single_leaf_trees(pot):
         assert np.array_equal(t.export_cell_index(), _expected_index(s))
 
 
-def test_index_toggle_and_limits(pot):
+def test_index_toggle_and_limits(pot, oracle_mod):
     sc = S.scene_random(89, 5, 2, p_occ=0.3)
     t = pot.Tree.from_scene(sc)
     full = t.info()
@@ -83,6 +83,18 @@ def test_index_toggle_and_limits(pot):
     with pytest.raises(pot.PotError) as e:
         td.set_cell_index(True)
     assert e.value.status == pot.POT_ERR_UNSUPPORTED
+    # rays aimed at the three leaves, rendered by the descent
+    import torch
+    h = 2.0 / 2048
+    vox = np.array([[5, 7, 9], [1000, 3, 1500], [2047, 2047, 0]], np.float64)
+    centres = (-1.0 + (vox + 0.5) * h).astype(np.float32)
+    o = np.repeat(centres + np.float32([0.0, 0.0, 3.0]), 11, axis=0)
+    jitter = (S.uniform(5, 1, np.arange(33 * 2, dtype=np.uint64)).reshape(33, 2) - 0.5) * 2e-3
+    d = np.concatenate([jitter, -np.ones((33, 1))], 1).astype(np.float32)
+    rgb = pot.render_rays(td, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()).cpu().numpy()
+    ref = oracle_mod.render_rays(oracle_mod.build_sparse(deep), o, d)["rgb"]
+    assert np.abs(rgb - ref).max() <= 1e-4
+    pot.check()
 
 
 def _both(pot, t, fn):
