@@ -162,12 +162,19 @@ pot_status pot_tree_free(pot_tree *tree);
 
 /* Cell index of a tree (the paper has no counterpart: an acceleration
  * structure of this library).  A dense int32 array over the 2^D grid that
- * gives, for every voxel, the leaf holding it (>= 0) or -(l + 1) for the empty
- * node of level l that contains it -- exactly what the descent of the child
- * array (Sec. 3.2 "Rendering") finds, so renders, gradients and visibility
- * weights are bit-identical with and without it; with it, locating each cell
- * is one 4-byte load instead of a descent.  Size 4 * 8^D bytes (537 MB at
- * D = 9, 4.3 GB at D = 10); only for D <= 10.
+ * gives, for every voxel, the leaf holding it (>= 0) -- what the descent of
+ * the child array (Sec. 3.2 "Rendering") finds -- or, for an empty voxel, a
+ * box of empty space around it that a ray crosses in one step:
+ *   -(2 + 2 l)   the empty octree node of level l that contains it, or
+ *   -(3 + 2 e)   the cube of (2e+1)^3 voxels centred on it (every voxel within
+ *                Chebyshev distance e is empty; e <= 63), recorded where
+ *                2e + 2 > 2^(D-l).
+ * A leaf's segment is bounded by the crossing times of its own faces however
+ * the empty space before it was stepped over, so renders, gradients and
+ * visibility weights are bit-identical with and without the index; with it,
+ * locating each cell is one 4-byte load instead of a descent and empty space
+ * takes fewer steps.  Size 4 * 8^D bytes (537 MB at D = 9, 4.3 GB at
+ * D = 10); only for D <= 10 (the build also needs 2 * 8^D bytes of scratch).
  *   Every tree of depth <= 10 that pot_build, pot_build_sparse,
  *   pot_tree_prune or pot_tree_quantize creates gets one when the device has
  *   room for it (pot_tree_info.index_bytes says whether it has).
@@ -178,9 +185,9 @@ pot_status pot_tree_free(pot_tree *tree);
  *   Not thread-safe against renders of the same tree from other host threads. */
 pot_status pot_tree_set_cell_index(pot_tree *tree, int32_t enable, pot_stream stream);
 
-/* The cell index as a dense [R][R][R] int32 array indexed [x][y][z] (R = 2^D)
- * into caller memory (host or device); POT_ERR_INVALID_ARG if the tree has
- * none.  (No counterpart in the paper.) */
+/* The cell index (entries as above) as a dense [R][R][R] int32 array indexed
+ * [x][y][z] (R = 2^D) into caller memory (host or device);
+ * POT_ERR_INVALID_ARG if the tree has none.  (No counterpart in the paper.) */
 pot_status pot_tree_export_cell_index(const pot_tree *tree, int32_t *out, pot_stream stream);
 
 /* ---------------------------------------------------------------- query ---

@@ -281,8 +281,9 @@ class Tree:
         _check(lib().pot_tree_set_cell_index(self.handle, 1 if enable else 0, _stream(stream)))
 
     def export_cell_index(self, stream=None) -> np.ndarray:
-        """``pot_tree_export_cell_index``: int32 [R, R, R] indexed [x][y][z]: leaf index, or
-        -(l + 1) for a voxel inside an empty node of level l."""
+        """``pot_tree_export_cell_index``: int32 [R, R, R] indexed [x][y][z]: leaf index; for an
+        empty voxel -(2 + 2 l) (inside the empty node of level l) or -(3 + 2 e) (every voxel within
+        Chebyshev distance e is empty)."""
         R = 1 << self.info()["depth"]
         out = np.zeros((R, R, R), np.int32)
         _check(lib().pot_tree_export_cell_index(self.handle, _ptr(out), _stream(stream)))

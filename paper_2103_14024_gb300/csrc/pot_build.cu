@@ -323,11 +323,62 @@ __global__ void k_cell_index(int D, const int32_t *child, int32_t *cells)
                     node = c;
                     continue;
                 }
-                v = c < 0 ? -c - 1 : -(l + 2);  // an empty slot of a level-l node is a level-(l+1) cell
+                // an empty slot of a level-l node is an empty level-(l+1) node
+                v = c < 0 ? -c - 1 : cell_code_node(l + 1);
                 break;
             }
         }
         cells[o] = v;
+    }
+}
+
+// Chebyshev distance transform of the occupied voxels, capped at
+// kCellCubeMax + 1, in three passes along x, y, z of an x-major uint8 grid
+// f (0 = occupied): f'(v) = min over |k| <= kCellCubeMax of max(|k|, f(v + k e_axis)).
+// The L-infinity distance separates into these 1-D passes; values beyond the
+// cap stay at the cap, a lower bound, which is all the renderer needs.
+constexpr int kDistCap = kCellCubeMax + 1;
+
+__global__ void k_dist_init(int D, const int32_t *cells, uint8_t *f)
+{
+    const int64_t n = 1ll << (3 * D);
+    const uint32_t m = (1u << D) - 1u;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
+        f[v] = cells[cell_index_offset(x, y, z, D)] >= 0 ? 0 : (uint8_t)kDistCap;
+    }
+}
+
+__global__ void k_dist_pass(int D, int axis, const uint8_t *in, uint8_t *out)
+{
+    const int64_t n = 1ll << (3 * D);
+    const int R = 1 << D;
+    const int shift = D * (2 - axis);  // x: 2D, y: D, z: 0
+    const int64_t stride = 1ll << shift;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)((v >> shift) & (R - 1));
+        int best = in[v];
+        for (int k = 1; k < best && k <= kCellCubeMax; ++k) {
+            if (c - k >= 0) best = min(best, max(k, (int)in[v - k * stride]));
+            if (c + k < R) best = min(best, max(k, (int)in[v + k * stride]));
+        }
+        out[v] = (uint8_t)best;
+    }
+}
+
+// Empty entries become cubes where the cube's half-extent e = distance - 1
+// is at least half the empty node's size (2e + 2 > 2^(D-l)).
+__global__ void k_dist_apply(int D, const uint8_t *f, int32_t *cells)
+{
+    const int64_t n = 1ll << (3 * D);
+    const uint32_t m = (1u << D) - 1u;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
+        int32_t &c = cells[cell_index_offset(x, y, z, D)];
+        if (c >= 0) continue;
+        const int level = (-c - 2) >> 1;
+        const int e = (int)f[v] - 1;
+        if (2 * e + 2 > (1 << (D - level))) c = cell_code_cube(e);
     }
 }
 
@@ -371,7 +422,26 @@ cudaError_t build_cell_index(pot_tree *t, cudaStream_t s)
         count_launch();
         e = cudaGetLastError();
     }
+    // empty cubes from the distance transform (two R^3 byte grids, freed here)
+    const int64_t nv = 1ll << (3 * D);
+    uint8_t *f0 = nullptr, *f1 = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync(&f0, (size_t)nv, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&f1, (size_t)nv, s);
+    if (e == cudaSuccess) {
+        const int64_t want = (nv + 255) / 256, cap = (int64_t)sms * 16;
+        const unsigned g = (unsigned)(want < cap ? want : cap);
+        k_dist_init<<<g, 256, 0, s>>>(D, cells, f0);
+        k_dist_pass<<<g, 256, 0, s>>>(D, 0, f0, f1);
+        k_dist_pass<<<g, 256, 0, s>>>(D, 1, f1, f0);
+        k_dist_pass<<<g, 256, 0, s>>>(D, 2, f0, f1);
+        k_dist_apply<<<g, 256, 0, s>>>(D, f1, cells);
+        count_launch(5);
+        e = cudaGetLastError();
+    }
+    if (f0) cudaFreeAsync(f0, s);
+    if (f1) cudaFreeAsync(f1, s);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
         cudaFree(cells);
         return e;
     }

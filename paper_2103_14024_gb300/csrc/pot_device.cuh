@@ -20,14 +20,22 @@ namespace pot {
 constexpr int kMaxDepth = 12;
 
 // ------------------------------------------------------------------------
-// cell index: for every voxel of the 2^D grid, the leaf that holds it (>= 0)
-// or -(level + 1) of the empty node that contains it, where an empty node of
-// level l spans 2^(D-l) voxels per axis.  Locating a cell (the octree descent
-// of Sec. 3.2 "Rendering") becomes one 4-byte load.  Entries are stored in
-// 4x4x4 bricks (bricks ordered x, y, z; inside a brick x, y, z), so that a
-// 128-byte line covers 2x4x4 voxels and neighbouring rays share lines.
+// cell index: for every voxel of the 2^D grid, the leaf that holds it (>= 0),
+// or, for an empty voxel, the empty box a ray may cross in one step:
+//   -(2 + 2 l)      the empty octree node of level l around the voxel
+//                   (2^(D-l) voxels per axis, aligned), or
+//   -(3 + 2 e)      the cube of (2e+1)^3 voxels centred on it, all empty
+//                   (e < the voxel's Chebyshev distance to the nearest leaf).
+// Locating a cell (the octree descent of Sec. 3.2 "Rendering") becomes one
+// 4-byte load, and empty space is crossed in steps of whichever box is larger.
+// Entries are stored in 4x4x4 bricks (bricks ordered x, y, z; inside a brick
+// x, y, z), so that a 128-byte line covers 2x4x4 voxels.
 // ------------------------------------------------------------------------
 constexpr int kCellIndexMaxDepth = 10;  // 4 * 8^10 bytes = 4.3 GB
+constexpr int kCellCubeMax = 63;        // largest cube half-extent e the build looks for
+
+__host__ __device__ __forceinline__ int32_t cell_code_node(int level) { return -(2 + 2 * level); }
+__host__ __device__ __forceinline__ int32_t cell_code_cube(int e) { return -(3 + 2 * e); }
 
 __host__ __device__ __forceinline__ uint32_t cell_index_offset(uint32_t x, uint32_t y, uint32_t z, int D)
 {

@@ -51,7 +51,10 @@ struct Walker {
     __device__ __forceinline__ SmemY<K, kBlock> Y() const { return {ysm}; }
     df t, tout;
     int q[3];
-    int leaf, cell_lvl, lvl_valid, step_i;
+    // cell: the box the ray is in, cshape >= 0: the cube of half-extent cshape
+    // centred on voxel q (a leaf is the cube of extent 0); cshape < 0: the
+    // aligned octree node of 2^(-cshape - 1) voxels per axis around q
+    int leaf, cshape, lvl_valid, step_i;
     int kx[3];
     df tcx[3];
 
@@ -59,13 +62,14 @@ struct Walker {
     // has one, else a descent from the deepest ancestor nq shares with voxel
     // pq (whose path the stack holds up to lvl_valid)
     __device__ __forceinline__ void descend(const RenderParams &p, int32_t *stk, const int nq[3], const int pq[3],
-                                            int &out_leaf, int &out_lvl)
+                                            int &out_leaf, int &out_shape)
     {
         const int D = p.depth;
         if (p.cells) {
             const int v = __ldg(p.cells + cell_index_offset((uint32_t)nq[0], (uint32_t)nq[1], (uint32_t)nq[2], D));
+            const int c = -v - 2;  // empty: 2 l (octree node of level l) or 2 e + 1 (cube of half-extent e)
             out_leaf = v >= 0 ? v : -1;
-            out_lvl = v >= 0 ? D : -v - 1;
+            out_shape = v >= 0 ? 0 : (c & 1) ? (c >> 1) : -(1 + D - (c >> 1));
             return;
         }
         const unsigned diff = (unsigned)((nq[0] ^ pq[0]) | (nq[1] ^ pq[1]) | (nq[2] ^ pq[2]));
@@ -73,7 +77,7 @@ struct Walker {
         int l = min(lc, lvl_valid);
         int node = stk[l * kBlock];
         out_leaf = -1;
-        out_lvl = D;
+        out_shape = 0;
         for (; l < D; ++l) {
             const int b = D - 1 - l;
             const int s = (((nq[0] >> b) & 1) << 2) | (((nq[1] >> b) & 1) << 1) | ((nq[2] >> b) & 1);
@@ -84,7 +88,7 @@ struct Walker {
                 continue;
             }
             if (c < 0) out_leaf = -c - 1;
-            else out_lvl = l + 1;
+            else out_shape = -(D - l);  // empty node of level l + 1: 2^(D-l-1) voxels per axis
             break;
         }
         lvl_valid = min(l, D - 1);
@@ -144,7 +148,7 @@ struct Walker {
         }
         lvl_valid = 0;
         if (!p.cells) stk[0] = 0;  // the stack exists only for trees without a cell index
-        descend(p, stk, q, q, leaf, cell_lvl);
+        descend(p, stk, q, q, leaf, cshape);
         if (POT_PREFETCH && leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
         // exit plane (voxel index) and crossing time per axis, recomputed only
         // when the plane changes (once per step inside runs of leaves)
@@ -162,14 +166,14 @@ struct Walker {
         const int D = p.depth;
         const int R = p.R;
         const float h = p.h, invh = p.invh;
-        // a4: exit of the current cell
-        const int sz = 1 << (D - cell_lvl);
+        // a4: exit of the current cell [qb, qb + sz) per axis
+        const int sz = cshape >= 0 ? 2 * cshape + 1 : 1 << (-cshape - 1);
         int qb[3];
         df texit = {__int_as_float(0x7f800000), 0.f};
         int ax = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            qb[a] = q[a] & ~(sz - 1);
+            qb[a] = cshape >= 0 ? q[a] - cshape : q[a] & ~(sz - 1);
             if (d[a] != 0.f) {
                 const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
                 if (k != kx[a]) {
@@ -189,10 +193,12 @@ struct Walker {
         // next voxel and its cell, fetched ahead of shading the current leaf:
         // the exit axis steps one cell; the other axes are located at t_exit
         // within the current cell's face (a one-voxel cell keeps them) and
-        // never move backwards
+        // never move backwards.  A leaf's entry time is the crossing time of
+        // its own face plane whichever box the ray crossed before it, so the
+        // leaf segments do not depend on how empty space was stepped over.
         bool stop = last;
         int nq[3] = {q[0], q[1], q[2]};
-        int nleaf = -1, nlvl = D;
+        int nleaf = -1, nshape = 0;
         if (!last) {
             if (step_i >= p.step_cap) {
                 atomicOr(p.err, 1u);
@@ -205,15 +211,16 @@ struct Walker {
                         nq[a] = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
                         outside = nq[a] < 0 || nq[a] >= R;
                     } else if (sz > 1 && d[a] != 0.f) {
+                        // within the cell and the grid (a cube may reach past the grid)
                         int v = locate_axis(texit, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
-                        v = min(max(v, qb[a]), qb[a] + sz - 1);
+                        v = min(max(v, max(qb[a], 0)), min(qb[a] + sz, R) - 1);
                         nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
                     }
                 }
                 if (outside) {
                     stop = true;
                 } else {
-                    descend(p, stk, nq, q, nleaf, nlvl);
+                    descend(p, stk, nq, q, nleaf, nshape);
                     if (POT_PREFETCH && nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
                 }
             }
@@ -225,7 +232,7 @@ struct Walker {
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[a] = nq[a];
         leaf = nleaf;
-        cell_lvl = nlvl;
+        cshape = nshape;
         if (df_lt(t, texit)) t = texit;
         ++step_i;
         return true;

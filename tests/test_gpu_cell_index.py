@@ -19,10 +19,17 @@ def pot():
     return P
 
 
+CUBE_MAX = 63   # largest cube half-extent the index records
+
+
 def _expected_index(sc):
     """Entry of every voxel [x][y][z] from the occupied Morton codes: the leaf
-    rank, else -(l + 1) for the coarsest level l whose block around the voxel
-    holds no occupied voxel (the empty child of an existing node)."""
+    rank; for an empty voxel, with l the coarsest level whose block around the
+    voxel holds no occupied voxel (the empty child of an existing node) and
+    dist its Chebyshev distance to the nearest occupied voxel (scipy, capped
+    at CUBE_MAX + 1): the cube code -(3 + 2e), e = dist - 1, if 2e + 2 > 2^(D-l),
+    else the node code -(2 + 2l)."""
+    from scipy import ndimage
     D, R = sc.depth, 1 << sc.depth
     g = np.arange(R, dtype=np.uint64)
     x, y, z = np.meshgrid(g, g, g, indexing="ij")
@@ -35,15 +42,27 @@ def _expected_index(sc):
         inside = np.isin(m >> sh, np.unique(occ >> sh))
         level[(level < 0) & ~inside] = l
     empty = level > 0
-    out[empty] = -(level[empty] + 1)
     out[~empty] = np.searchsorted(occ, m[~empty])
+    grid_empty = empty.reshape(R, R, R)
+    if grid_empty.all():
+        dist = np.full(grid_empty.shape, CUBE_MAX + 1)
+    else:
+        dist = np.minimum(ndimage.distance_transform_cdt(grid_empty, metric="chessboard"), CUBE_MAX + 1)
+    e = dist.ravel()[empty] - 1
+    lv = level[empty]
+    cube = 2 * e + 2 > (1 << (D - lv))
+    out[empty] = np.where(cube, -(3 + 2 * e), -(2 + 2 * lv))
     return out.reshape(R, R, R).astype(np.int32)
 
 
 @pytest.mark.parametrize("seed,D,p_occ", [(81, 1, 0.5), (82, 2, 0.3), (83, 3, 0.2), (84, 4, 0.05),
-                                          (85, 5, 0.3), (86, 6, 0.02), (87, 7, 0.01)])
+                                          (85, 5, 0.3), (86, 6, 0.02), (87, 7, 0.01), (80, 7, 0.0)])
 def test_index_entries_match_definition(pot, seed, D, p_occ):
     sc = S.scene_random(seed, D, 1, p_occ=p_occ)
+    if p_occ == 0.0:   # one occupied voxel in a corner: distances past the cap
+        sc = S.scene_random(seed, D, 1, p_occ=0.01)
+        keep = np.argmin(sc.morton)
+        sc = sc.replace(morton=sc.morton[keep:keep + 1], sigma=sc.sigma[keep:keep + 1], sh=sc.sh[keep:keep + 1])
     t = pot.Tree.from_scene(sc)
     info = t.info()
     assert info["index_bytes"] == 4 * max(64, 8 ** D)
