@@ -248,27 +248,35 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
     gh = torch.zeros((L, K, 3), dtype=torch.float32, device="cuda")
     B = args.train_batch
     gen = torch.Generator(device="cuda").manual_seed(1003)
-    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in ("bwd", "step")}
-    losses, t_bwd, t_step = [], [], []
+    parts = ("batch", "forward", "mse", "zero", "backward", "optimizer")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
+    losses, t_parts = [], {k: [] for k in parts}
     n_total = args.train_steps + 3
     for it in range(n_total):
-        ev["step"][0].record()
+        ev[0].record()
         idx = torch.randint(0, all_o.shape[0], (B,), device="cuda", generator=gen)
+        if args.train_sort:   # same random rays, in view / row / column order: coherent warps
+            idx = torch.sort(idx).values
         o, d, y = all_o[idx], all_d[idx], target[idx]
+        ev[1].record()
         rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
+        ev[2].record()
         loss, g = pot.loss_mse(rgb, y)
+        ev[3].record()
         gs.zero_()
         gh.zero_()
-        ev["bwd"][0].record()
+        ev[4].record()
         pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0, far=6.0)
-        ev["bwd"][1].record()
+        ev[5].record()
         opt.step(gs, gh)
-        ev["step"][1].record()
+        ev[6].record()
         torch.cuda.synchronize()
         losses.append(float(loss.item()))
         if it >= 3:
-            t_bwd.append(ev["bwd"][0].elapsed_time(ev["bwd"][1]))
-            t_step.append(ev["step"][0].elapsed_time(ev["step"][1]))
+            for k, name in enumerate(parts):
+                t_parts[name].append(ev[k].elapsed_time(ev[k + 1]))
+    t_bwd = t_parts["backward"]
+    t_step = [sum(v) for v in zip(*t_parts.values())]
     pot.check()
     tree.free()
     mb, ms = sum(t_bwd) / len(t_bwd), sum(t_step) / len(t_step)
@@ -277,7 +285,9 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
             "lr_sh": args.train_lr_sh, "steps": args.train_steps,
             "bwd_mrays_s": round(B / (mb * 1e-3) / 1e6, 2), "bwd_ms": round(mb, 4),
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
-            "step_parts": "random batch + gather (torch), forward, MSE, zero grads (torch), backward, optimiser step",
+            "step_parts": ("random batch" + (" sorted by pixel" if args.train_sort else "") +
+                           " + gather (torch), forward, MSE, zero grads (torch), backward, optimiser step"),
+            "parts_ms": {k: round(sum(v) / len(v), 4) for k, v in t_parts.items()},
             "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6)}
 
 
@@ -355,6 +365,9 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--train-steps", type=int, default=30)
     ap.add_argument("--train-batch", type=int, default=1 << 18)
+    ap.add_argument("--train-sort", type=int, default=1,
+                    help="1: order each random ray batch by view and pixel before rendering (the sum of the "
+                         "gradients does not depend on the order)")
     ap.add_argument("--train-opt", default="rmsprop", choices=["sgd", "rmsprop", "adam"])
     ap.add_argument("--train-lr-sigma", type=float, default=1.0)
     ap.add_argument("--train-lr-sh", type=float, default=1e-2)

@@ -169,7 +169,48 @@ struct StepParams {
     float bc1, bc2;  // Adam bias corrections 1 - beta^t
 };
 
+// One parameter's update; m and v are its optimiser state (v unused by SGD,
+// m only by Adam).
 template <int KIND>
+__device__ __forceinline__ float step_one(const StepParams &sp, float x, float g, float lr, float &m, float &v)
+{
+    if (KIND == POT_SGD) {
+        x -= lr * g;
+    } else if (KIND == POT_RMSPROP) {
+        v = sp.alpha * v + (1.f - sp.alpha) * g * g;
+        x -= lr * g / (sqrtf(v) + sp.eps);
+    } else {
+        m = sp.beta1 * m + (1.f - sp.beta1) * g;
+        v = sp.beta2 * v + (1.f - sp.beta2) * g * g;
+        x -= (lr / sp.bc1) * m / (sqrtf(v) / sqrtf(sp.bc2) + sp.eps);
+    }
+    return x;
+}
+
+// State of value j (public order: sigma part, then SH part): RMSprop v at
+// state[j]; Adam m at state[j], v at state[N + j].
+template <int KIND>
+__device__ __forceinline__ void load_state(const float *state, int64_t N, int64_t j, float &m, float &v)
+{
+    if (KIND == POT_RMSPROP) v = state[j];
+    if (KIND == POT_ADAM) {
+        m = state[j];
+        v = state[N + j];
+    }
+}
+template <int KIND>
+__device__ __forceinline__ void store_state(float *state, int64_t N, int64_t j, float m, float v)
+{
+    if (KIND == POT_RMSPROP) state[j] = v;
+    if (KIND == POT_ADAM) {
+        state[j] = m;
+        state[N + j] = v;
+    }
+}
+
+// FLAT: the SH records have no padding (stride == 3K), so the public
+// gradient index is the record index and no division is needed.
+template <int KIND, bool FLAT>
 __global__ void k_step(StepParams sp, float *sigma, float *sh, const float *gs, const float *gsh, float *state)
 {
     const int64_t N = sp.L * (1 + sp.K3);
@@ -182,28 +223,62 @@ __global__ void k_step(StepParams sp, float *sigma, float *sh, const float *gs, 
             lr = sp.lr_sigma;
         } else {
             const int64_t jj = j - sp.L;
-            const int64_t i = jj / sp.K3;
-            param = sh + i * sp.stride + (jj - i * sp.K3);
+            if (FLAT) {
+                param = sh + jj;
+            } else {
+                const int64_t i = jj / sp.K3;
+                param = sh + i * sp.stride + (jj - i * sp.K3);
+            }
             g = gsh[jj];
             lr = sp.lr_sh;
         }
-        float x = *param;
-        if (KIND == POT_SGD) {
-            x -= lr * g;
-        } else if (KIND == POT_RMSPROP) {
-            float v = state[j];
-            v = sp.alpha * v + (1.f - sp.alpha) * g * g;
-            state[j] = v;
-            x -= lr * g / (sqrtf(v) + sp.eps);
+        float m = 0.f, v = 0.f;
+        load_state<KIND>(state, N, j, m, v);
+        *param = step_one<KIND>(sp, *param, g, lr, m, v);
+        store_state<KIND>(state, N, j, m, v);
+    }
+}
+
+// The same update with 16-byte accesses for the SH part (unpadded records,
+// L a multiple of 4, 16-byte aligned arrays): the step streams ~5 arrays of
+// L (1 + 3K) floats and is bound by HBM.
+template <int KIND>
+__global__ void k_step_vec(StepParams sp, float *sigma, float4 *sh4, const float *gs, const float4 *gsh4,
+                           float *state)
+{
+    const int64_t N = sp.L * (1 + sp.K3);
+    const int64_t n4 = sp.L * sp.K3 / 4;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < sp.L + n4;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (j < sp.L) {
+            float m = 0.f, v = 0.f;
+            load_state<KIND>(state, N, j, m, v);
+            sigma[j] = step_one<KIND>(sp, sigma[j], gs[j], sp.lr_sigma, m, v);
+            store_state<KIND>(state, N, j, m, v);
         } else {
-            float m = state[j], v = state[N + j];
-            m = sp.beta1 * m + (1.f - sp.beta1) * g;
-            v = sp.beta2 * v + (1.f - sp.beta2) * g * g;
-            state[j] = m;
-            state[N + j] = v;
-            x -= (lr / sp.bc1) * m / (sqrtf(v) / sqrtf(sp.bc2) + sp.eps);
+            const int64_t u = j - sp.L;
+            float4 x = sh4[u];
+            const float4 g = gsh4[u];
+            float4 *m4 = nullptr, *v4 = nullptr;  // Adam m, v / RMSprop v (in m4)
+            if (KIND != POT_SGD) m4 = reinterpret_cast<float4 *>(state + sp.L) + u;
+            if (KIND == POT_ADAM) v4 = reinterpret_cast<float4 *>(state + N + sp.L) + u;
+            float4 m = make_float4(0.f, 0.f, 0.f, 0.f), v = m;
+            if (KIND == POT_RMSPROP) v = *m4;
+            if (KIND == POT_ADAM) {
+                m = *m4;
+                v = *v4;
+            }
+            x.x = step_one<KIND>(sp, x.x, g.x, sp.lr_sh, m.x, v.x);
+            x.y = step_one<KIND>(sp, x.y, g.y, sp.lr_sh, m.y, v.y);
+            x.z = step_one<KIND>(sp, x.z, g.z, sp.lr_sh, m.z, v.z);
+            x.w = step_one<KIND>(sp, x.w, g.w, sp.lr_sh, m.w, v.w);
+            sh4[u] = x;
+            if (KIND == POT_RMSPROP) *m4 = v;
+            if (KIND == POT_ADAM) {
+                *m4 = m;
+                *v4 = v;
+            }
         }
-        *param = x;
     }
 }
 
@@ -295,9 +370,23 @@ cudaError_t launch_step(pot_tree *t, int kind, float lr_sigma, float lr_sh, floa
     const unsigned g = grid_n(sp.L * (1 + sp.K3));
     float *sig = static_cast<float *>(t->sigma);
     float *sh = static_cast<float *>(t->sh);
-    if (kind == POT_SGD) k_step<POT_SGD><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
-    else if (kind == POT_RMSPROP) k_step<POT_RMSPROP><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
-    else k_step<POT_ADAM><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
+    const bool flat = sp.stride == sp.K3;
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    const bool vec = flat && sp.L % 4 == 0 && a16(sh) && a16(gsh) && (kind == POT_SGD || a16(state));
+    const unsigned gv = grid_n(sp.L + sp.L * sp.K3 / 4);
+#define POT_STEP(KIND)                                                                           \
+    if (vec) k_step_vec<KIND><<<gv, 256, 0, s>>>(sp, sig, reinterpret_cast<float4 *>(sh), gs,    \
+                                                  reinterpret_cast<const float4 *>(gsh), state); \
+    else if (flat) k_step<KIND, true><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);            \
+    else k_step<KIND, false><<<g, 256, 0, s>>>(sp, sig, sh, gs, gsh, state);
+    if (kind == POT_SGD) {
+        POT_STEP(POT_SGD)
+    } else if (kind == POT_RMSPROP) {
+        POT_STEP(POT_RMSPROP)
+    } else {
+        POT_STEP(POT_ADAM)
+    }
+#undef POT_STEP
     count_launch();
     return cudaGetLastError();
 }

@@ -94,9 +94,15 @@ def test_backward_tiny_with_early_stop(pot, oracle_mod, torch_mod):
 
 
 @pytest.mark.parametrize("kind", ["sgd", "rmsprop", "adam"])
-def test_step_vs_oracle(pot, oracle_mod, torch_mod, kind):
+@pytest.mark.parametrize("deg,rem", [(2, 0), (3, 0), (3, 1), (1, 2)])
+def test_step_vs_oracle(pot, oracle_mod, torch_mod, kind, deg, rem):
+    """deg 2: padded SH records (27 of 28 floats); deg 3 / 1: unpadded records,
+    with the leaf count a multiple of 4 (16-byte update path) or not."""
     torch = torch_mod
-    sc = S.scene_random(57, 4, 2, p_occ=0.4)
+    sc = S.scene_random(57, 4, deg, p_occ=0.4)
+    n = sc.n - (sc.n % 4) + rem if sc.n % 4 >= rem else sc.n - (sc.n % 4) - 4 + rem
+    sc = sc.replace(morton=sc.morton[:n], sigma=sc.sigma[:n], sh=sc.sh[:n])
+    assert sc.n % 4 == rem
     t = pot.Tree.from_scene(sc)
     L, K = sc.n, sc.sh_dim
     rng = np.random.default_rng(3)
