@@ -35,8 +35,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 1.8443 GB read + 0.1231 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "8b1dc2e6b1829b4c", "bytes_per_launch": 24.592e9},
+    # 16-view capture (one view group): 1.9903 GB read + 0.1180 GB written, x 12.5 = 200-view launch
+    "f32": {"sha": "218c3d47853c56cc", "bytes_per_launch": 26.354e9},
 }
 
 
