@@ -88,7 +88,44 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Stream-ordered temporary device buffer.
+}  // namespace
+
+// Stream-ordered scratch of the library comes from a memory pool per device
+// that keeps up to 1 GiB of freed memory for the next call; the default pool
+// returns freed memory at every synchronisation, so each host-output render
+// re-mapped its staging buffers (about 9 ms per 200-view call).
+cudaError_t pot::scratch_pool(cudaMemPool_t *out)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = 1ull << 30;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
+namespace {
+
+// Stream-ordered temporary device buffer (from the library's scratch pool).
 struct Tmp {
     void *p = nullptr;
     cudaStream_t s = nullptr;
@@ -99,7 +136,10 @@ struct Tmp {
     cudaError_t alloc(size_t bytes, cudaStream_t st)
     {
         s = st;
-        return cudaMallocAsync(&p, bytes > 0 ? bytes : 16, st);
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = scratch_pool(&pool);
+        if (e != cudaSuccess) return e;
+        return cudaMallocFromPoolAsync(&p, bytes > 0 ? bytes : 16, pool, st);
     }
 };
 
@@ -320,20 +360,22 @@ cudaError_t launch_render(const RenderParams &p, const pot_tree *t, bool cams, c
 }
 
 // Per-device stream for device->host copies that overlap rendering.
-cudaError_t copy_stream(cudaStream_t *out)
+// Library-owned streams per device: 0 = copies of host outputs, 1 = second
+// render stream of host-output renders.
+cudaError_t aux_stream(int which, cudaStream_t *out)
 {
     static std::mutex mu;
-    static cudaStream_t st[64] = {nullptr};
+    static cudaStream_t st[2][64] = {{nullptr}};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(mu);
-    if (!st[dev]) {
-        e = cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking);
+    if (!st[which][dev]) {
+        e = cudaStreamCreateWithFlags(&st[which][dev], cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
     }
-    *out = st[dev];
+    *out = st[which][dev];
     return cudaSuccess;
 }
 
@@ -344,35 +386,46 @@ cudaError_t copy_stream(cudaStream_t *out)
 pot_status render_to_host(RenderParams p, const pot_tree *t, const pot_camera *d_cams, int n_cams, float *rgb,
                           float *t_final, cudaStream_t s)
 {
+    // view groups render alternately on s and a second stream (so one group's
+    // last tiles overlap the next group's first) into two staging buffers,
+    // whose copies to the host run on a copy stream while later groups render
     const int64_t per_cam = (int64_t)p.W * p.H;
     const int chunk = render_view_group(n_cams);
     const int n_chunks = (n_cams + chunk - 1) / chunk;
     const bool rgb_dev = is_device_ptr(rgb);
     const bool tf_dev = t_final && is_device_ptr(t_final);
-    cudaStream_t cs;
-    POT_CUDA(copy_stream(&cs), "copy stream");
+    cudaStream_t cs, rs[2];
+    POT_CUDA(aux_stream(0, &cs), "copy stream");
+    POT_CUDA(aux_stream(1, &rs[1]), "render stream");
+    rs[0] = s;
     Tmp stage[2], stage_tf[2];
-    cudaEvent_t rendered[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+    cudaEvent_t rendered[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr}, start = nullptr;
     struct Events {
-        cudaEvent_t *a, *b;
+        cudaEvent_t *a, *b, *c;
         ~Events()
         {
             for (int i = 0; i < 2; ++i) {
                 if (a[i]) cudaEventDestroy(a[i]);
                 if (b[i]) cudaEventDestroy(b[i]);
             }
+            if (*c) cudaEventDestroy(*c);
         }
-    } guard{rendered, copied};
+    } guard{rendered, copied, &start};
     for (int i = 0; i < 2; ++i) {
         POT_CUDA(cudaEventCreateWithFlags(&rendered[i], cudaEventDisableTiming), "event");
         POT_CUDA(cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming), "event");
         if (!rgb_dev) POT_CUDA(stage[i].alloc(sizeof(float) * 3 * per_cam * chunk, s), "alloc stage");
         if (t_final && !tf_dev) POT_CUDA(stage_tf[i].alloc(sizeof(float) * per_cam * chunk, s), "alloc stage");
     }
+    // the second render stream starts after everything queued on s so far
+    // (tile counters, cameras, staging allocations)
+    POT_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming), "event");
+    POT_CUDA(cudaEventRecord(start, s), "record");
+    POT_CUDA(cudaStreamWaitEvent(rs[1], start, 0), "wait start");
     for (int c = 0; c < n_chunks; ++c) {
         const int b = c & 1;
         const int c0 = c * chunk, nc = std::min(chunk, n_cams - c0);
-        if (c >= 2) POT_CUDA(cudaStreamWaitEvent(s, copied[b], 0), "wait copy");
+        if (c >= 2) POT_CUDA(cudaStreamWaitEvent(rs[b], copied[b], 0), "wait copy");
         RenderParams q = p;
         q.cams = d_cams + c0;
         q.n_cams = nc;
@@ -381,8 +434,8 @@ pot_status render_to_host(RenderParams p, const pot_tree *t, const pot_camera *d
         q.rgb = rgb_dev ? rgb + 3 * per_cam * c0 : static_cast<float *>(stage[b].p);
         q.t_final = !t_final ? nullptr : (tf_dev ? t_final + per_cam * c0 : static_cast<float *>(stage_tf[b].p));
         q.tile_counter = p.tile_counter + c;
-        POT_CUDA(launch_render(q, t, true, s), "render");
-        POT_CUDA(cudaEventRecord(rendered[b], s), "record");
+        POT_CUDA(launch_render(q, t, true, rs[b]), "render");
+        POT_CUDA(cudaEventRecord(rendered[b], rs[b]), "record");
         POT_CUDA(cudaStreamWaitEvent(cs, rendered[b], 0), "wait render");
         if (!rgb_dev)
             POT_CUDA(cudaMemcpyAsync(rgb + 3 * per_cam * c0, stage[b].p, sizeof(float) * 3 * per_cam * nc,
@@ -395,6 +448,7 @@ pot_status render_to_host(RenderParams p, const pot_tree *t, const pot_camera *d
         POT_CUDA(cudaEventRecord(copied[b], cs), "record");
     }
     // the staging buffers are released on s: make s wait for the last copies
+    // (which follow every render of both streams)
     for (int b = 0; b < 2 && b < n_chunks; ++b) POT_CUDA(cudaStreamWaitEvent(s, copied[b], 0), "wait copy");
     POT_CUDA(cudaStreamSynchronize(s), "sync");
     return POT_OK;

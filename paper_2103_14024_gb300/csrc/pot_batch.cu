@@ -164,7 +164,9 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
     const size_t cnt_bytes = 256;
     const size_t bytes = cnt_bytes + sizeof(BatchItem) * (size_t)n;
     void *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(&pool);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&buf, bytes, pool, s);
     if (e != cudaSuccess) return e;
     char *cb = static_cast<char *>(buf);
     BatchItem *d_items = reinterpret_cast<BatchItem *>(cb + cnt_bytes);

@@ -117,6 +117,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
 int render_view_group(int n_cams);
 
 unsigned int *device_error_word();   // per-device word raised by kernels
+cudaError_t scratch_pool(cudaMemPool_t *out);  // the library's pool of stream-ordered scratch
 void set_last_error(const char *msg); // message returned by pot_last_error on this thread
 void count_launch(int n = 1);
 
