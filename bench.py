@@ -247,6 +247,7 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
     gs = torch.zeros(L, dtype=torch.float32, device="cuda")
     gh = torch.zeros((L, K, 3), dtype=torch.float32, device="cuda")
     B = args.train_batch
+    loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
     gen = torch.Generator(device="cuda").manual_seed(1003)
     parts = ("batch", "forward", "mse", "zero", "backward", "optimizer")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
@@ -259,14 +260,24 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
             idx = torch.sort(idx).values
         o, d, y = all_o[idx], all_d[idx], target[idx]
         ev[1].record()
-        rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
-        ev[2].record()
-        loss, g = pot.loss_mse(rgb, y)
-        ev[3].record()
-        gs.zero_()
-        gh.zero_()
-        ev[4].record()
-        pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0, far=6.0)
+        if args.train_fused:   # render + MSE + backward in one launch
+            ev[2].record()
+            ev[3].record()
+            gs.zero_()
+            gh.zero_()
+            ev[4].record()
+            loss, _, _ = pot.render_mse_backward(tree, o, d, y, grad_sigma=gs, grad_sh=gh, loss=loss_buf,
+                                                 gamma=GAMMA, near=2.0, far=6.0)
+        else:
+            rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
+            ev[2].record()
+            loss, g = pot.loss_mse(rgb, y)
+            ev[3].record()
+            gs.zero_()
+            gh.zero_()
+            ev[4].record()
+            pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0,
+                                far=6.0)
         ev[5].record()
         opt.step(gs, gh)
         ev[6].record()
@@ -284,9 +295,14 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
             "rays_per_batch": B, "optimizer": args.train_opt, "lr_sigma": args.train_lr_sigma,
             "lr_sh": args.train_lr_sh, "steps": args.train_steps,
             "bwd_mrays_s": round(B / (mb * 1e-3) / 1e6, 2), "bwd_ms": round(mb, 4),
+            "bwd_launch": ("pot_render_mse_backward: colour walk + MSE + gradient walk" if args.train_fused
+                           else "pot_render_backward with the forward colour given"),
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
             "step_parts": ("random batch" + (" sorted by pixel" if args.train_sort else "") +
-                           " + gather (torch), forward, MSE, zero grads (torch), backward, optimiser step"),
+                           " + gather (torch), " +
+                           ("zero grads (torch), fused forward + MSE + backward (one launch), "
+                            if args.train_fused else "forward, MSE, zero grads (torch), backward, ") +
+                           "optimiser step"),
             "parts_ms": {k: round(sum(v) / len(v), 4) for k, v in t_parts.items()},
             "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6)}
 
@@ -371,6 +387,9 @@ def main():
     ap.add_argument("--train-sort", type=int, default=1,
                     help="1: order each random ray batch by view and pixel before rendering (the sum of the "
                          "gradients does not depend on the order)")
+    ap.add_argument("--train-fused", type=int, default=0,
+                    help="1: pot_render_mse_backward (render, loss and gradients in one launch); "
+                         "0: pot_render_rays + pot_loss_mse + pot_render_backward")
     ap.add_argument("--train-opt", default="rmsprop", choices=["sgd", "rmsprop", "adam"])
     ap.add_argument("--train-lr-sigma", type=float, default=1.0)
     ap.add_argument("--train-lr-sh", type=float, default=1e-2)

@@ -234,6 +234,20 @@ pot_status pot_render_backward(const pot_tree *tree, int64_t n, const float *ori
                                const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
                                float *grad_sigma, float *grad_sh, pot_stream stream);
 
+/* Sec. 3.3 / App. B.3.2 in one launch, for a training batch: each ray is
+ * rendered as by pot_render_rays (C, same opts), the MSE loss
+ *   L = sum over rays and channels of (C - target)^2 / (3 n)
+ * (the loss of pot_loss_mse) is WRITTEN to *loss (one float), and its
+ * gradients (pot_render_backward with grad_rgb = 2 (C - target) / (3 n)) are
+ * ACCUMULATED into grad_sigma [n_leaves] and grad_sh [n_leaves][K][3].  rgb
+ * [n][3] receives C when not NULL.  Each ray is walked twice in the same
+ * launch (colour, then gradients), so no colour buffer or second launch is
+ * needed.  target [n][3] float32; every array in device memory.  Float atomic
+ * summation order (gradients, loss) is not deterministic.                  */
+pot_status pot_render_mse_backward(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
+                                   const float *target, const pot_render_opts *opts, float *rgb, float *loss,
+                                   float *grad_sigma, float *grad_sh, pot_stream stream);
+
 /* ----------------------------------------------------------------- step ---
  * Sec. 3.3 / App. B.5: gradient step on the leaf values with the structure
  * fixed (the paper uses SGD; RMSprop and Adam are offered too), in place on a

@@ -92,6 +92,7 @@ _SIGS = {
     "pot_render_rays": [_p, C.c_int64, _p, _p, _p, _p, _p, _p],
     "pot_check": [_p],
     "pot_render_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p],
+    "pot_render_mse_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p, _p],
     "pot_step": [_p, _p, _p, _p, _p, _p],
     "pot_loss_mse": [C.c_int64, _p, _p, _p, _p, _p],
     "pot_camera_rays": [_p, C.c_int32, C.c_int64, _p, _p, _p, _p],
@@ -385,6 +386,27 @@ def render_backward(tree: Tree, origins, dirs, grad_rgb, rgb_fwd=None, grad_sigm
     _check(lib().pot_render_backward(tree.handle, int(origins.shape[0]), _ptr(origins), _ptr(dirs), _ptr(grad_rgb),
                                      _ptr(rgb_fwd), C.byref(o), _ptr(grad_sigma), _ptr(grad_sh), _stream(stream)))
     return grad_sigma, grad_sh
+
+
+def render_mse_backward(tree: Tree, origins, dirs, target, grad_sigma=None, grad_sh=None, rgb=None, loss=None,
+                        bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0, far=3.0e38, stream=None):
+    """``pot_render_mse_backward``: renders the rays, writes the MSE against ``target`` to ``loss``
+    (a 1-element device tensor) and accumulates its gradients; returns (loss, grad_sigma, grad_sh)."""
+    import torch
+    inf = tree.info()
+    L, K = inf["n_leaves"], inf["sh_dim"]
+    dev = origins.device
+    if grad_sigma is None:
+        grad_sigma = torch.zeros(L, dtype=torch.float32, device=dev)
+    if grad_sh is None:
+        grad_sh = torch.zeros((L, K, 3), dtype=torch.float32, device=dev)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    o = _opts(bg, gamma, near, far)
+    _check(lib().pot_render_mse_backward(tree.handle, int(origins.shape[0]), _ptr(origins), _ptr(dirs),
+                                         _ptr(target), C.byref(o), _ptr(rgb), _ptr(loss), _ptr(grad_sigma),
+                                         _ptr(grad_sh), _stream(stream)))
+    return loss, grad_sigma, grad_sh
 
 
 def step_state_floats(tree: Tree, kind: str) -> int:

@@ -969,6 +969,47 @@ pot_status pot_render_backward(const pot_tree *t, int64_t n, const float *origin
     return POT_OK;
 }
 
+pot_status pot_render_mse_backward(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
+                                   const float *target, const pot_render_opts *opts, float *rgb, float *loss,
+                                   float *grad_sigma, float *grad_sh, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
+    if (!loss || !is_device_ptr(loss)) return fail(POT_ERR_INVALID_ARG, "loss must be device memory");
+    if (n == 0) return POT_OK;
+    const bool leaves = t->n_leaves > 0;
+    if (!origins || !dirs || !target || (leaves && (!grad_sigma || !grad_sh)))
+        return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(origins) || !is_device_ptr(dirs) || !is_device_ptr(target) ||
+        (leaves && (!is_device_ptr(grad_sigma) || !is_device_ptr(grad_sh))) || (rgb && !is_device_ptr(rgb)))
+        return fail(POT_ERR_INVALID_ARG, "pot_render_mse_backward takes device arrays only");
+    pot_status st = check_opts(opts);
+    if (st != POT_OK) return st;
+    if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
+    if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp scratch;
+    POT_CUDA(scratch.alloc(sizeof(unsigned long long), s), "alloc scratch");
+    POT_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), s), "memset");
+    POT_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), s), "memset loss");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.ray_o = origins;
+    p.ray_d = dirs;
+    p.n_rays = n;
+    p.near = near;
+    p.far = far;
+    p.n_tiles = (n + 31) / 32;
+    p.tile_counter = static_cast<unsigned long long *>(scratch.p);
+    POT_CUDA(launch_mse_backward(p, target, rgb, loss, grad_sigma, grad_sh, t->desc.leaf_dtype, t->K, s),
+             "mse backward");
+    return POT_OK;
+}
+
 int64_t pot_step_state_floats(const pot_tree *t, int32_t kind)
 {
     if (!t) return -1;

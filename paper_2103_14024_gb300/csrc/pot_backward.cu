@@ -84,13 +84,24 @@ struct BackwardParams {
     const float *rgb_fwd;  // NULL: computed by a first pass
     float *grad_sigma;
     float *grad_sh;
+    // fused MSE mode: dL/dC = mse_scale (C - target), L += sum (C - target)^2 mse_scale / 2
+    const float *target;
+    float *loss;
+    float *rgb_out;        // optional copy of C
+    float mse_scale;
 };
+
+// What the backward kernel is given per ray.
+enum BackwardMode { kGradAndColour = 0, kGrad = 1, kMseTarget = 2 };
 
 #ifndef POT_BACKWARD_MIN_BLOCKS
 #define POT_BACKWARD_MIN_BLOCKS 2  // 3 blocks/SM spill the gradient visitor's state (measured 10 % slower)
 #endif
 
-template <int K, typename T, bool HAVE_FWD>
+// MODE kGradAndColour: dL/dC and C given; kGrad: dL/dC given, C from a first
+// walk; kMseTarget: C from a first walk, then dL/dC of the MSE against the
+// target, the loss summed per warp into *loss, C optionally written out.
+template <int K, typename T, int MODE>
 __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kernel(const BackwardParams bp)
 {
     POT_WALK_SHARED(K)
@@ -104,6 +115,7 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= (unsigned long long)p.n_tiles) break;
         const int64_t ray = (int64_t)tile * 32 + lane;
+        float lsum = 0.f;  // this ray's squared error (MSE mode)
         if (ray < p.n_rays) {
             float o[3], d[3];
 #pragma unroll
@@ -119,11 +131,8 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
             gv.grad_sigma = bp.grad_sigma;
             gv.grad_sh = bp.grad_sh;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                gv.g[c] = __ldg(bp.grad_rgb + 3 * ray + c);
-                gv.prefix[c] = 0.f;
-            }
-            if (HAVE_FWD) {
+            for (int c = 0; c < 3; ++c) gv.prefix[c] = 0.f;
+            if (MODE == kGradAndColour) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(bp.rgb_fwd + 3 * ray + c);
             } else {
@@ -132,19 +141,39 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = fmaf(sv.Tr, p.bg[c], sv.col[c]);
             }
+            if (MODE == kMseTarget) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float r = gv.ctot[c] - __ldg(bp.target + 3 * ray + c);
+                    lsum = fmaf(r, r, lsum);
+                    gv.g[c] = bp.mse_scale * r;
+                    if (bp.rgb_out) bp.rgb_out[3 * ray + c] = gv.ctot[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) gv.g[c] = __ldg(bp.grad_rgb + 3 * ray + c);
+            }
             if (gv.g[0] != 0.f || gv.g[1] != 0.f || gv.g[2] != 0.f)
                 walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, p.near, p.far, gv);
+        }
+        if (MODE == kMseTarget) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if (lane == 0 && lsum != 0.f) atomicAdd(bp.loss, 0.5f * bp.mse_scale * lsum);
         }
     }
 }
 
 template <typename T>
-cudaError_t launch_backward_t(const BackwardParams &bp, int K, bool have_fwd, cudaStream_t s)
+cudaError_t launch_backward_t(const BackwardParams &bp, int K, int mode, cudaStream_t s)
 {
     using Fn = void (*)(const BackwardParams);
     Fn fn = nullptr;
-#define POT_PICK(KK) \
-    if (K == KK) fn = have_fwd ? backward_kernel<KK, T, true> : backward_kernel<KK, T, false>;
+#define POT_PICK(KK)                                                                              \
+    if (K == KK)                                                                                  \
+        fn = mode == kGradAndColour ? backward_kernel<KK, T, kGradAndColour>                      \
+             : mode == kGrad        ? backward_kernel<KK, T, kGrad>                               \
+                                    : backward_kernel<KK, T, kMseTarget>;
     POT_PICK(1)
     POT_PICK(4)
     POT_PICK(9)
@@ -343,11 +372,24 @@ unsigned grid_n(int64_t n)
 cudaError_t launch_backward(const RenderParams &r, const float *grad_rgb, const float *rgb_fwd, float *grad_sigma,
                             float *grad_sh, int dtype, int K, cudaStream_t s)
 {
-    BackwardParams bp{r, grad_rgb, rgb_fwd, grad_sigma, grad_sh};
+    BackwardParams bp{r, grad_rgb, rgb_fwd, grad_sigma, grad_sh, nullptr, nullptr, nullptr, 0.f};
+    const int mode = rgb_fwd ? kGradAndColour : kGrad;
     switch (dtype) {
-    case POT_F32: return launch_backward_t<float>(bp, K, rgb_fwd != nullptr, s);
-    case POT_F16: return launch_backward_t<__half>(bp, K, rgb_fwd != nullptr, s);
-    default: return launch_backward_t<__nv_bfloat16>(bp, K, rgb_fwd != nullptr, s);
+    case POT_F32: return launch_backward_t<float>(bp, K, mode, s);
+    case POT_F16: return launch_backward_t<__half>(bp, K, mode, s);
+    default: return launch_backward_t<__nv_bfloat16>(bp, K, mode, s);
+    }
+}
+
+cudaError_t launch_mse_backward(const RenderParams &r, const float *target, float *rgb_out, float *loss,
+                                float *grad_sigma, float *grad_sh, int dtype, int K, cudaStream_t s)
+{
+    BackwardParams bp{r, nullptr, nullptr, grad_sigma, grad_sh, target, loss, rgb_out,
+                      2.f / (3.f * (float)r.n_rays)};
+    switch (dtype) {
+    case POT_F32: return launch_backward_t<float>(bp, K, kMseTarget, s);
+    case POT_F16: return launch_backward_t<__half>(bp, K, kMseTarget, s);
+    default: return launch_backward_t<__nv_bfloat16>(bp, K, kMseTarget, s);
     }
 }
 

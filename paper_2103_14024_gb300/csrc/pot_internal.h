@@ -101,6 +101,8 @@ cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaS
 
 cudaError_t launch_backward(const RenderParams &r, const float *grad_rgb, const float *rgb_fwd, float *grad_sigma,
                             float *grad_sh, int dtype, int K, cudaStream_t s);
+cudaError_t launch_mse_backward(const RenderParams &r, const float *target, float *rgb_out, float *loss,
+                                float *grad_sigma, float *grad_sh, int dtype, int K, cudaStream_t s);
 cudaError_t launch_step(pot_tree *t, int kind, float lr_sigma, float lr_sh, float alpha, float beta1, float beta2,
                         float eps, int step, const float *gs, const float *gsh, float *state, cudaStream_t s);
 cudaError_t launch_mse(int64_t n, const float *rgb, const float *target, float *grad, float *loss, cudaStream_t s);

@@ -62,6 +62,43 @@ def test_backward_vs_oracle(pot, oracle_mod, torch_mod, seed, D, deg, bg):
     pot.check()
 
 
+@pytest.mark.parametrize("seed,D,deg,dtype", [(61, 4, 1, "f32"), (62, 5, 3, "f32"), (63, 5, 2, "f16")])
+def test_mse_backward_fused(pot, oracle_mod, torch_mod, seed, D, deg, dtype):
+    """pot_render_mse_backward = pot_render_rays + pot_loss_mse + pot_render_backward in one
+    launch; its gradients also against the oracle's, with the oracle's own MSE gradient."""
+    torch = torch_mod
+    sc = S.scene_random(seed, D, deg, p_occ=0.35, sigma_mu=1.5, sigma_s=1.0, sh_std=0.8)
+    t = pot.Tree.from_scene(sc, dtype=dtype)
+    ot = oracle_mod.build_sparse(sc, dtype=dtype)
+    o, d = S.random_rays(seed, 2503, radius=3.0, spread=0.9)
+    target = np.random.default_rng(seed).uniform(size=(o.shape[0], 3)).astype(np.float32)
+    og, od, tg = (torch.from_numpy(a).cuda() for a in (o, d, target))
+    bg = (0.2, 0.3, 0.4)
+    rgb = torch.full((o.shape[0], 3), -1.0, device="cuda")
+    loss, gs, gh = pot.render_mse_backward(t, og, od, tg, rgb=rgb, bg=bg, gamma=1e-3, near=0.2, far=8.0)
+    ref_rgb = pot.render_rays(t, og, od, bg=bg, gamma=1e-3, near=0.2, far=8.0)
+    assert torch.equal(rgb, ref_rgb)                       # the same walk and arithmetic
+    ref_loss, g = pot.loss_mse(ref_rgb, tg)
+    assert abs(float(loss.item()) - float(ref_loss.item())) <= 1e-5 * float(ref_loss.item())
+    rs_, rh_ = pot.render_backward(t, og, od, g, rgb_fwd=ref_rgb, bg=bg, gamma=1e-3, near=0.2, far=8.0)
+    assert torch.allclose(gs, rs_, rtol=1e-5, atol=1e-7) and torch.allclose(gh, rh_, rtol=1e-5, atol=1e-7)
+    # against the oracle (gamma = 0: no stop decision to share): its colour, its MSE
+    # gradient 2 (C - target) / (3 n), its adjoint
+    loss, gs, gh = pot.render_mse_backward(t, og, od, tg, bg=bg, near=0.2, far=8.0)
+    ref = oracle_mod.render_rays(ot, o, d, near=0.2, far=8.0, bg=bg)["rgb"]
+    g64 = 2.0 * (ref - target.astype(np.float64)) / (3 * o.shape[0])
+    rs, rh = oracle_mod.backward_rays(ot, o, d, g64, near=0.2, far=8.0, bg=bg)
+    _close(gs.cpu().numpy(), rs, "fused grad_sigma")
+    _close(gh.cpu().numpy(), rh, "fused grad_sh")
+    assert abs(float(loss.item()) - float(((ref - target) ** 2).mean())) <= 1e-4 * float(((ref - target) ** 2).mean())
+    # an empty tree: background colour, loss only
+    empty = sc.replace(morton=sc.morton[:0], sigma=sc.sigma[:0], sh=sc.sh[:0])
+    te = pot.Tree.from_scene(empty, dtype=dtype)
+    le, _, _ = pot.render_mse_backward(te, og, od, tg, bg=bg)
+    assert abs(float(le.item()) - float(((np.float32(bg) - target) ** 2).mean())) <= 1e-5
+    pot.check()
+
+
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
 def test_backward_low_precision_trees(pot, oracle_mod, torch_mod, dtype):
     torch = torch_mod
