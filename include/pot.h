@@ -38,6 +38,11 @@
  * library detects which); when an output is in host memory the call
  * synchronises the stream before returning.  Inputs are read-only and owned by
  * the caller; trees are owned by the library and released by pot_tree_free.
+ * Per-call scratch (tile counters, staged inputs, staging buffers of host
+ * outputs) is stream-ordered memory from a pool the library keeps per device,
+ * which holds on to up to 1 GiB of freed scratch for later calls; host-output
+ * renders also use two library-owned streams per device (a second render
+ * stream and a copy stream) and join them back to the caller's stream.
  *
  * Errors.  Every entry point returns a pot_status; POT_OK is 0.  The message
  * of the last failure on the calling thread is returned by pot_last_error().
