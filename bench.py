@@ -15,7 +15,6 @@ and the output image in host memory (copies inside the timed region).
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -40,9 +39,17 @@ NCU_TRAFFIC = {
 }
 
 
+# the files compiled into the render kernel (a change anywhere else in the
+# library leaves its DRAM counters valid)
+KERNEL_SOURCES = ("csrc/pot_device.cuh", "csrc/pot_internal.h", "csrc/pot_render.cuh", "csrc/pot_render_f32.cu",
+                  "csrc/pot_render_f16.cu", "csrc/pot_render_bf16.cu", "csrc/pot_render_cb16.cu")
+
+
 def kernel_sha() -> str:
+    """Hash of the render kernel's sources and the public header."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2103_14024_gb300", "csrc", "*"))):
+    files = [os.path.join(ROOT, "paper_2103_14024_gb300", f) for f in KERNEL_SOURCES]
+    for f in files + [os.path.join(ROOT, "include", "pot.h")]:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())
             h.update(fh.read())
