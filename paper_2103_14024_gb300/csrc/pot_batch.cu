@@ -2,7 +2,7 @@
 // resolutions and outputs (the work list of a continuous-batching server).
 //
 // The host groups the items by (SH coefficients, leaf dtype); each group is one
-// launch.  Every item contributes ceil(W/8) * ceil(H/4) tiles of 8 x 4 pixels;
+// launch.  Every item contributes tiles of kTileW x kTileH pixels (as pot_render);
 // warps take tiles from one counter and find their item by binary search over
 // the items' first-tile offsets.  The per-ray code (walk + shading) is the
 // same as pot_render's, so a request renders bit-identically alone or in a mix.
@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
         const int64_t rem = (int64_t)tile - it.tile_begin;
         const int ty = (int)(rem / it.tiles_x);
         const int tx = (int)(rem - (int64_t)ty * it.tiles_x);
-        const int i = tx * 8 + (lane & 7);
-        const int j = ty * 4 + (lane >> 3);
+        const int i = tx * kTileW + (lane % kTileW);
+        const int j = ty * kTileH + (lane / kTileW);
         if (i < it.W && j < it.H) {
             RenderParams p;
             p.child = it.child;
@@ -152,12 +152,12 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         b.gamma = r.gamma;
         b.W = r.cam.width;
         b.H = r.cam.height;
-        b.tiles_x = (b.W + 7) / 8;
+        b.tiles_x = (b.W + kTileW - 1) / kTileW;
         b.tile_begin = tiles;
         b.rgb = r.rgb;
         b.t_final = r.t_final;
         b.cam = r.cam;
-        tiles += (int64_t)b.tiles_x * ((b.H + 3) / 4);
+        tiles += (int64_t)b.tiles_x * ((b.H + kTileH - 1) / kTileH);
     }
     group_start.push_back(n);
     const int groups = (int)group_start.size() - 1;
@@ -178,7 +178,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         BatchParams bp;
         bp.items = d_items + a;
         bp.n_items = b - a;
-        bp.n_tiles = last.tile_begin + (int64_t)last.tiles_x * ((last.H + 3) / 4);
+        bp.n_tiles = last.tile_begin + (int64_t)last.tiles_x * ((last.H + kTileH - 1) / kTileH);
         bp.tile_counter = reinterpret_cast<unsigned long long *>(cb) + g;
         bp.err = err;
         const pot_tree *t = items[order[a]].tree;

@@ -319,6 +319,43 @@ def test_traversal_step_bound_raises_error_word(pot, torch_mod):
     pot.check()
 
 
+def test_render_tile_limit_is_an_error(pot, torch_mod):
+    """A call whose tiles would reach 2^32 is refused before any launch (the
+    kernels index tiles in 32 bits); the image is never touched."""
+    t = pot.Tree.from_scene(S.scene_tiny())
+    big = S.make_cameras(S.orbit_c2ws(65, radius=3.0), 46000, 46000, 40000.0)   # 65 x 2^26 tiles
+    rgb = torch_mod.full((4,), -1.0, device="cuda")
+    with pytest.raises(pot.PotError) as e:
+        pot.render(t, big, rgb=rgb)
+    assert e.value.status == pot.POT_ERR_INVALID_ARG
+    assert torch_mod.equal(rgb, torch_mod.full((4,), -1.0, device="cuda"))
+    pot.check()
+
+
+def test_render_depth_12_tree(pot, oracle_mod, torch_mod):
+    """The deepest trees (D = 12, 4096^3 voxels, no cell index): rays through
+    single leaves far apart, against the oracle."""
+    D = 12
+    xyz = np.array([[3, 4, 5], [2048, 100, 4095], [4095, 4095, 4095], [1000, 1001, 1002]], np.uint64)
+    m = S.morton_encode(xyz[:, 0], xyz[:, 1], xyz[:, 2], D)
+    order = np.argsort(m)
+    sc = S.Scene(depth=D, bbox_lo=(-1.0, -1.0, -1.0), bbox_size=2.0, sh_degree=1, morton=m[order].astype(np.uint64),
+                 sigma=np.float32([900.0, 2000.0, 500.0, 1500.0]),
+                 sh=np.random.default_rng(0).normal(size=(4, 4, 3)).astype(np.float32))
+    t = pot.Tree.from_scene(sc)
+    assert t.info()["index_bytes"] == 0
+    h = 2.0 / 4096
+    centres = (-1.0 + (xyz[order].astype(np.float64) + 0.5) * h).astype(np.float32)
+    o = np.repeat(centres - np.float32([0.0, 0.0, 2.5]), 7, axis=0)
+    jit = (S.uniform(12, 1, np.arange(2 * o.shape[0], dtype=np.uint64)).reshape(-1, 2) - 0.5) * (1.5 * h / 2.5)
+    d = np.concatenate([jit, np.ones((o.shape[0], 1))], 1).astype(np.float32)
+    rgb = pot.render_rays(t, torch_mod.from_numpy(o).cuda(), torch_mod.from_numpy(d).cuda()).cpu().numpy()
+    ref = oracle_mod.render_rays(oracle_mod.build_sparse(sc), o, d)["rgb"]
+    assert np.abs(rgb - ref).max() <= TOL
+    assert (np.abs(ref).sum(1) > 0).sum() >= 4          # some rays do hit the leaves
+    pot.check()
+
+
 def test_render_invalid_args(pot):
     sc = S.scene_tiny()
     t = pot.Tree.from_scene(sc)
