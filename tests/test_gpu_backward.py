@@ -62,6 +62,47 @@ def test_backward_vs_oracle(pot, oracle_mod, torch_mod, seed, D, deg, bg):
     pot.check()
 
 
+def test_backward_vs_gpu_finite_differences(pot, torch_mod):
+    """The adjoint against central differences of the GPU render itself, on a
+    depth-5 copy of the main scene: L = sum over rays of <g, C>, each sampled
+    leaf value moved by +-eps through pot_tree_set_values."""
+    torch = torch_mod
+    sc = S.scene_shapes(depth=5, sh_degree=3)
+    t = pot.Tree.from_scene(sc)
+    cams = S.make_cameras(S.orbit_c2ws(3, radius=4.0), 48, 48, 60.0, near=2.0, far=6.0)
+    o, d = pot.camera_rays(cams)
+    g = torch.from_numpy(np.random.default_rng(9).normal(size=(o.shape[0], 3)).astype(np.float32)).cuda()
+    gs, gh = pot.render_backward(t, o, d, g, near=2.0, far=6.0)
+    sig0 = torch.from_numpy(sc.sigma.astype(np.float32)).cuda()
+    sh0 = torch.from_numpy(sc.sh.astype(np.float32)).cuda()
+
+    def loss(sig, sh):
+        t.set_values(sig, sh)
+        return float((pot.render_rays(t, o, d, near=2.0, far=6.0).double() * g.double()).sum().item())
+
+    checked = 0
+    for which, grad in (("sigma", gs), ("sh", gh)):
+        flat = grad.reshape(-1).abs()
+        for idx in torch.topk(flat, 4).indices.tolist():
+            sig, sh = sig0.clone(), sh0.clone()
+            base = (sig if which == "sigma" else sh).reshape(-1)
+            x = float(base[idx].item())
+            if which == "sigma" and x < 1.0:
+                continue
+            eps = 1e-3 * max(1.0, abs(x))
+            base[idx] = x + eps
+            lp = loss(sig, sh)
+            base[idx] = x - eps
+            lm = loss(sig, sh)
+            fd = (lp - lm) / (2 * eps)
+            an = float(grad.reshape(-1)[idx].item())
+            assert abs(fd - an) <= 2e-2 * abs(an) + 1e-3, (which, idx, fd, an)
+            checked += 1
+    t.set_values(sig0, sh0)
+    assert checked >= 6
+    pot.check()
+
+
 @pytest.mark.parametrize("seed,D,deg,dtype", [(61, 4, 1, "f32"), (62, 5, 3, "f32"), (63, 5, 2, "f16")])
 def test_mse_backward_fused(pot, oracle_mod, torch_mod, seed, D, deg, dtype):
     """pot_render_mse_backward = pot_render_rays + pot_loss_mse + pot_render_backward in one
