@@ -173,7 +173,16 @@ def summarize(requests, wall: float | None = None) -> dict:
     t_end = max(r.t_done for r in requests)
     t_start = min(r.arrival for r in requests)
     span = wall if wall is not None else (t_end - t_start)
+    by_res = {}
+    for r, l in zip(requests, lat):
+        by_res.setdefault(f"{int(r.cam['width'])}x{int(r.cam['height'])}", []).append(l)
     return {"requests": len(requests), "rejected": rejected, "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
             "max_ms": round(float(lat.max()), 3), "rays": int(rays),
-            "mrays_s": round(rays / span / 1e6, 2), "span_s": round(span, 4)}
+            "mrays_s": round(rays / span / 1e6, 2), "span_s": round(span, 4),
+            "by_resolution": {k: {"n": len(v), "p50_ms": round(float(np.percentile(v, 50)), 3),
+                                  "p99_ms": round(float(np.percentile(v, 99)), 3)}
+                              for k, v in sorted(by_res.items())},
+            # arrival -> launch (queueing + admission + host work) and launch -> completion seen
+            "p50_wait_ms": round(float(np.percentile([(r.t_launch - r.arrival) * 1e3 for r in requests], 50)), 3),
+            "p50_run_ms": round(float(np.percentile([(r.t_done - r.t_launch) * 1e3 for r in requests], 50)), 3)}
