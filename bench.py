@@ -209,16 +209,17 @@ def algorithmic_bytes(pot, torch, tree, cams, dtype, leaf_bytes):
     touched = torch.zeros(n_leaves, dtype=torch.uint8, device="cuda")
     seg = torch.zeros((1, H, W), dtype=torch.int32, device="cuda")
     rgb = torch.empty((1, H, W, 3), dtype=torch.float32, device="cuda")
-    uniq, segs = 0, 0
+    uniq, segs, hits = 0, 0, 0
     for v in range(len(cams)):
         touched.zero_()
         pot.render(tree, cams[v:v + 1], rgb=rgb, gamma=GAMMA, seg_count=seg, leaf_touched=touched)
         uniq += int(touched.sum().item())
         segs += int(seg.sum().item())
+        hits += int((seg > 0).sum().item())
     rays = len(cams) * W * H
     out_bytes = 12 * rays
     return {"unique_leaves": uniq, "leaf_segments": segs, "hbm_bytes": uniq * leaf_bytes + out_bytes,
-            "touched_bytes": segs * leaf_bytes + out_bytes, "rays": rays}
+            "touched_bytes": segs * leaf_bytes + out_bytes, "rays": rays, "hit_rays": hits}
 
 
 def l2_read_peak(torch):
@@ -491,6 +492,7 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "ms_per_step_median": round(sorted(main_res["per"])[len(main_res["per"]) // 2], 3),
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": dict(workload_config(scene, args.dtype, len(cams)),
                        cell_index_bytes=int(main_res["info"]["index_bytes"])),
@@ -513,7 +515,9 @@ def main():
             line["l2"] = {"error": str(e)}
         line["counts"] = {"unique_leaves_summed_over_views": alg["unique_leaves"],
                           "leaf_segments": alg["leaf_segments"],
-                          "mean_leaf_segments_per_ray": round(alg["leaf_segments"] / rays, 3)}
+                          "mean_leaf_segments_per_ray": round(alg["leaf_segments"] / rays, 3),
+                          "hit_fraction": round(alg["hit_rays"] / rays, 4),
+                          "mean_leaf_segments_per_hit_ray": round(alg["leaf_segments"] / max(1, alg["hit_rays"]), 3)}
     if not args.no_e2e:
         e2e_value = world * rays / main_res["e2e_wall"] / 1e6
         line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * len(cams),
@@ -548,6 +552,15 @@ def main():
         line["cpu_baseline"] = {"value": round(rate / 1e6, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
                                 "sample": f"all pixels of views 0,2,...,198 of 200 ({n} rays, {dt:.1f} s on "
                                           f"{thr} threads)"}
+        # the same oracle on one thread, all pixels of view 0
+        from oracle import oracle
+        oracle.set_num_threads(1)
+        try:
+            rate1, n1, dt1, _ = run_oracle_timing(scene, synth.cameras_main(N_VIEWS, W, H), [0], 1)
+        finally:
+            oracle.set_num_threads(thr)
+        line["cpu_baseline"]["value_1_thread"] = round(rate1 / 1e6, 4)
+        line["cpu_baseline"]["sample_1_thread"] = f"all pixels of view 0 ({n1} rays, {dt1:.1f} s)"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
