@@ -34,8 +34,8 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 1.9903 GB read + 0.1180 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "218c3d47853c56cc", "bytes_per_launch": 26.354e9},
+    # 16-view capture (one view group): 2.0017 GB read + 0.1181 GB written, x 12.5 = 200-view launch
+    "f32": {"sha": "44186fb39d496f71", "bytes_per_launch": 26.498e9},
 }
 
 
