@@ -281,12 +281,16 @@ class Tree:
         that replaces the child-array descent when locating cells (depth <= 10)."""
         _check(lib().pot_tree_set_cell_index(self.handle, 1 if enable else 0, _stream(stream)))
 
-    def export_cell_index(self, stream=None) -> np.ndarray:
+    def export_cell_index(self, device=None, stream=None):
         """``pot_tree_export_cell_index``: int32 [R, R, R] indexed [x][y][z]: leaf index; for an
         empty voxel -(2 + 2 l) (inside the empty node of level l) or -(3 + 2 e) (every voxel within
-        Chebyshev distance e is empty)."""
+        Chebyshev distance e is empty).  numpy by default; a torch tensor on ``device`` if given."""
         R = 1 << self.info()["depth"]
-        out = np.zeros((R, R, R), np.int32)
+        if device is None:
+            out = np.zeros((R, R, R), np.int32)
+        else:
+            import torch
+            out = torch.empty((R, R, R), dtype=torch.int32, device=device)
         _check(lib().pot_tree_export_cell_index(self.handle, _ptr(out), _stream(stream)))
         return out
 

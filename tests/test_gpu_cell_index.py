@@ -69,6 +69,58 @@ def test_index_entries_match_definition(pot, seed, D, p_occ):
     assert np.array_equal(t.export_cell_index(), _expected_index(sc))
 
 
+def test_index_depth_10(pot, oracle_mod):
+    """The largest indexed depth (1024^3 voxels, 4.3 GB): sampled entries against
+    their definition (Chebyshev distance by brute force over the occupied voxels,
+    node level from Morton prefixes), and renders through the tree against the
+    oracle."""
+    import torch
+    D, R = 10, 1024
+    rng = np.random.default_rng(10)
+    # clusters of occupied voxels so that distances vary from 1 past the cap
+    centres = rng.integers(40, R - 40, size=(40, 3))
+    pts = (centres[:, None, :] + rng.integers(-6, 7, size=(40, 60, 3))).reshape(-1, 3)
+    m = np.unique(S.morton_encode(pts[:, 0].astype(np.uint64), pts[:, 1].astype(np.uint64),
+                                  pts[:, 2].astype(np.uint64), D))
+    n = m.shape[0]
+    sc = S.Scene(depth=D, bbox_lo=(-1.0, -1.0, -1.0), bbox_size=2.0, sh_degree=1, morton=m.astype(np.uint64),
+                 sigma=rng.uniform(50.0, 400.0, n).astype(np.float32),
+                 sh=rng.normal(size=(n, 4, 3)).astype(np.float32))
+    t = pot.Tree.from_scene(sc)
+    assert t.info()["index_bytes"] == 4 * 8 ** D
+    idx = t.export_cell_index(device="cuda")
+    x, y, z = (a.astype(np.int64) for a in S.morton_decode(sc.morton, D))
+    occ = np.stack([x, y, z], 1)
+    # sample voxels: near the clusters, and anywhere
+    near = (occ[rng.integers(0, n, 3000)] + rng.integers(-70, 71, size=(3000, 3))).clip(0, R - 1)
+    anyw = rng.integers(0, R, size=(1000, 3))
+    q = np.concatenate([near, anyw])
+    got = idx[torch.from_numpy(q[:, 0]).cuda(), torch.from_numpy(q[:, 1]).cuda(),
+              torch.from_numpy(q[:, 2]).cuda()].cpu().numpy()
+    mq = S.morton_encode(q[:, 0].astype(np.uint64), q[:, 1].astype(np.uint64), q[:, 2].astype(np.uint64), D)
+    for k in range(q.shape[0]):
+        pos = np.searchsorted(sc.morton, mq[k])
+        if pos < n and sc.morton[pos] == mq[k]:
+            assert got[k] == pos
+            continue
+        dist = min(int(np.abs(occ - q[k]).max(1).min()), CUBE_MAX + 1)
+        level = next(l for l in range(1, D + 1)
+                     if not np.any((sc.morton >> np.uint64(3 * (D - l))) == (mq[k] >> np.uint64(3 * (D - l)))))
+        e = dist - 1
+        want = -(3 + 2 * e) if 2 * e + 2 > (1 << (D - level)) else -(2 + 2 * level)
+        assert got[k] == want, (q[k], got[k], want)
+    del idx
+    # rays aimed at occupied voxels, against the oracle
+    h = 2.0 / R
+    tgt = (-1.0 + (occ[rng.integers(0, n, 300)] + 0.5) * h).astype(np.float32)
+    o = np.repeat(np.float32([[0.1, -3.5, 0.4]]), 300, axis=0)
+    d = (tgt - o).astype(np.float32)
+    rgb = pot.render_rays(t, torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()).cpu().numpy()
+    ref = oracle_mod.render_rays(oracle_mod.build_sparse(sc), o, d)["rgb"]
+    assert np.abs(rgb - ref).max() <= 1e-4
+    pot.check()
+
+
 def test_index_empty_and_single_leaf_trees(pot):
     sc = S.scene_random(88, 4, 0, p_occ=0.3)
     for n in (0, 1):
