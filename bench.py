@@ -36,6 +36,9 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 NCU_TRAFFIC = {
     # 16-view capture (one view group): 2.0017 GB read + 0.1181 GB written, x 12.5 = 200-view launch
     "f32": {"sha": "44186fb39d496f71", "bytes_per_launch": 26.498e9},
+    # fp16 leaves: 0.6090 GB read + 0.1088 GB written per 16 views; codebook leaves: 0.2843 + 0.1001 GB
+    "f16": {"sha": "44186fb39d496f71", "bytes_per_launch": 8.972e9},
+    "cb16": {"sha": "44186fb39d496f71", "bytes_per_launch": 4.806e9},
 }
 
 
