@@ -43,7 +43,15 @@ constexpr int kBlock = 256;
 // leaf prefetched before vis runs on the current one.
 template <int K, typename T>
 struct Walker {
-    float d[3], rd[3], Ahi[3], Alo[3], margin[3];
+    float d[3];
+    // per-ray constants in shared memory (this thread's column, stride kBlock):
+    // A = lo - o as hi + lo parts, 1/d, and the locate margins -- 12 registers
+    // fewer across the walk, which keeps 4 blocks of 256 threads per SM without spills
+    float *st;
+    __device__ __forceinline__ float Ahi(int a) const { return st[a * kBlock]; }
+    __device__ __forceinline__ float Alo(int a) const { return st[(3 + a) * kBlock]; }
+    __device__ __forceinline__ float rd(int a) const { return st[(6 + a) * kBlock]; }
+    __device__ __forceinline__ float margin(int a) const { return st[(9 + a) * kBlock]; }
     float len;
     // the per-ray SH basis lives in shared memory (this thread's part of the
     // block's array), not in 16 registers: that lets 4 blocks (32 warps) reside per SM
@@ -111,8 +119,11 @@ struct Walker {
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            two_sum(p.lo[a], -o[a], Ahi[a], Alo[a]);
-            rd[a] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
+            float ah, al;
+            two_sum(p.lo[a], -o[a], ah, al);
+            st[a * kBlock] = ah;
+            st[(3 + a) * kBlock] = al;
+            st[(6 + a) * kBlock] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
         }
         // a2: clip range in units of the ray parameter t (position o + t d)
         df tin = {near * invlen, 0.f};
@@ -125,8 +136,8 @@ struct Walker {
                 const bool inside = (s > 0.f || (s == 0.f && e >= 0.f)) && (s < p.size || (s == p.size && e < 0.f));
                 if (!inside) return false;
             } else {
-                df t0 = cross_time(0, h, Ahi[a], Alo[a], d[a], rd[a]);
-                df t1 = cross_time(R, h, Ahi[a], Alo[a], d[a], rd[a]);
+                df t0 = cross_time(0, h, Ahi(a), Alo(a), d[a], rd(a));
+                df t1 = cross_time(R, h, Ahi(a), Alo(a), d[a], rd(a));
                 if (d[a] < 0.f) {
                     df tmp = t0;
                     t0 = t1;
@@ -140,10 +151,10 @@ struct Walker {
         // error bound of the fp32 voxel-coordinate estimate, in voxels
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            margin[a] = (fabsf(tout.hi * d[a]) + fabsf(Ahi[a])) * invh * 3.8146973e-6f + 1e-6f;
+            st[(9 + a) * kBlock] = (fabsf(tout.hi * d[a]) + fabsf(Ahi(a))) * invh * 3.8146973e-6f + 1e-6f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            int v = locate_axis(tin, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+            int v = locate_axis(tin, d[a], Ahi(a), Alo(a), h, invh, margin(a));
             q[a] = min(max(v, 0), R - 1);
         }
         lvl_valid = 0;
@@ -178,7 +189,7 @@ struct Walker {
                 const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
                 if (k != kx[a]) {
                     kx[a] = k;
-                    tcx[a] = cross_time(k, h, Ahi[a], Alo[a], d[a], rd[a]);
+                    tcx[a] = cross_time(k, h, Ahi(a), Alo(a), d[a], rd(a));
                 }
                 if (df_lt(tcx[a], texit)) {
                     texit = tcx[a];
@@ -212,7 +223,7 @@ struct Walker {
                         outside = nq[a] < 0 || nq[a] >= R;
                     } else if (sz > 1 && d[a] != 0.f) {
                         // within the cell and the grid (a cube may reach past the grid)
-                        int v = locate_axis(texit, d[a], Ahi[a], Alo[a], h, invh, margin[a]);
+                        int v = locate_axis(texit, d[a], Ahi(a), Alo(a), h, invh, margin(a));
                         v = min(max(v, max(qb[a], 0)), min(qb[a] + sz, R) - 1);
                         nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
                     }
@@ -239,13 +250,15 @@ struct Walker {
     }
 };
 
-// Per-thread scratch of a walk in shared memory: the SH basis (SmemY) and
-// the ancestor stack [kMaxDepth][kBlock] in dynamic shared memory, which a
-// launch provides (walk_smem_bytes) only when some tree of it has no cell
-// index; without it the space goes to L1.  Declared once per kernel.
+// Per-thread scratch of a walk in shared memory: the SH basis (SmemY, rows
+// 0..K-1) and the walker's per-ray constants (rows K..K+11) of one
+// [K + 12][kBlock] float array, and the ancestor stack [kMaxDepth][kBlock] in
+// dynamic shared memory, which a launch provides (walk_smem_bytes) only when
+// some tree of it has no cell index; without it the space goes to L1.
+// Declared once per kernel.
 #define POT_WALK_SHARED(K)                                          \
     extern __shared__ int32_t walk_stack_sh[];                      \
-    __shared__ float ysm_sh[(K)][kBlock];                           \
+    __shared__ float ysm_sh[(K) + 12][kBlock];                      \
     int32_t *stk = walk_stack_sh + threadIdx.x;                     \
     float *ysm = &ysm_sh[0][threadIdx.x];                           \
     (void)ysm;
@@ -282,6 +295,7 @@ __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr
 {
     Walker<K, T> w;
     w.ysm = ysm;
+    w.st = ysm + (K) * kBlock;
     if (!w.begin(p, stk, sig_arr, sh_arr, o, d, near, far)) return;
     while (w.step(p, stk, sig_arr, sh_arr, vis)) {
     }
