@@ -34,11 +34,11 @@ N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 # DRAM bytes per render launch from the committed ncu capture (see
 # profiles/); reported only while the kernel sources still hash to ``sha``.
 NCU_TRAFFIC = {
-    # 16-view capture (one view group): 2.0017 GB read + 0.1181 GB written, x 12.5 = 200-view launch
-    "f32": {"sha": "44186fb39d496f71", "bytes_per_launch": 26.498e9},
-    # fp16 leaves: 0.6090 GB read + 0.1088 GB written per 16 views; codebook leaves: 0.2843 + 0.1001 GB
-    "f16": {"sha": "44186fb39d496f71", "bytes_per_launch": 8.972e9},
-    "cb16": {"sha": "44186fb39d496f71", "bytes_per_launch": 4.806e9},
+    # 16-view captures (one view group) x 12.5 = the 200-view launch:
+    # f32 1.9951 GB read + 0.1175 GB written; fp16 0.6095 + 0.1084; codebook 0.2839 + 0.1001
+    "f32": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 26.407e9},
+    "f16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 8.974e9},
+    "cb16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 4.800e9},
 }
 
 
