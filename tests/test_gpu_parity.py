@@ -252,6 +252,16 @@ def test_render_host_output_chunked(pot, torch_mod, pinned):
     host2 = torch.full((41, 21, 33, 3), -1.0)
     pot.render(t, cams, rgb=host2, t_final=dev_tf, gamma=1e-4)
     assert torch.equal(host2, ref.cpu()) and torch.equal(dev_tf, ref_tf)
+    # device rgb with a host t_final (the image is written in place, t_final staged)
+    dev_rgb = torch.full((41, 21, 33, 3), -1.0, device="cuda")
+    host_tf2 = torch.full((41, 21, 33), -1.0, pin_memory=pinned)
+    pot.render(t, cams, rgb=dev_rgb, t_final=host_tf2, gamma=1e-4)
+    assert torch.equal(dev_rgb, ref) and torch.equal(host_tf2, ref_tf.cpu())
+    # repeated calls reuse the library's scratch pool and streams: same result
+    for _ in range(3):
+        host.fill_(-1.0)
+        pot.render(t, cams, rgb=host, gamma=1e-4)
+        assert torch.equal(host, ref.cpu())
 
 
 def test_render_edge_cases(pot, oracle_mod, torch_mod):
