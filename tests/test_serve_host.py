@@ -99,3 +99,20 @@ def test_oversized_request_rejected_not_stuck():
     rej = [r for r in reqs if r.rejected]
     assert rej and all(r.rays * 12 > big - 1 for r in rej)
     assert all(r.t_done >= 0 for r in reqs)
+
+
+def test_summary_breakdowns_are_consistent():
+    """Per-resolution groups partition the requests, and the queue/run split
+    adds up to the latency of each request."""
+    reqs = _requests(200, rate=3000.0, seed=11)
+    srv, _ = _server(10 ** 10)
+    srv.run(reqs, mode="batch")
+    s = summarize(reqs)
+    assert sum(v["n"] for v in s["by_resolution"].values()) == s["requests"] == 200
+    for key, v in s["by_resolution"].items():
+        w, h = (int(x) for x in key.split("x"))
+        lat = [(r.t_done - r.arrival) * 1e3 for r in reqs if (int(r.cam["width"]), int(r.cam["height"])) == (w, h)]
+        assert v["n"] == len(lat) and abs(v["p50_ms"] - float(np.percentile(lat, 50))) < 1e-3
+    for r in reqs:
+        assert r.arrival <= r.t_admit <= r.t_launch <= r.t_done
+    assert s["p50_wait_ms"] >= 0 and s["p50_run_ms"] > 0
