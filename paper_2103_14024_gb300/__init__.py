@@ -89,6 +89,7 @@ _SIGS = {
     "pot_query": [_p, C.c_int64, _p, _p, _p],
     "pot_sh_basis": [C.c_int32, C.c_int64, _p, _p, _p],
     "pot_render": [_p, _p, C.c_int32, _p, _p, _p, _p],
+    "pot_render_noalloc": [_p, _p, C.c_int32, _p, _p, _p, _p],
     "pot_render_rays": [_p, C.c_int64, _p, _p, _p, _p, _p, _p],
     "pot_check": [_p],
     "pot_render_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p],
@@ -347,6 +348,17 @@ def render(tree: Tree, cams, rgb=None, t_final=None, bg=(0.0, 0.0, 0.0), gamma=0
     o = _opts(bg, gamma, seg_count=seg_count, leaf_touched=leaf_touched, max_steps=max_steps)
     _check(lib().pot_render(tree.handle, carr, n, C.byref(o), _ptr(rgb), _ptr(t_final), _stream(stream)))
     return (rgb, t_final) if want_t_final else rgb
+
+
+def render_noalloc(tree: Tree, cams, rgb, t_final=None, bg=(0.0, 0.0, 0.0), gamma=0.0, max_steps=0, stream=None):
+    """``pot_render_noalloc``: as ``render`` into caller-allocated device tensors, with no GPU
+    allocation inside the call (at most 1024 cameras; calls that overlap on the GPU must be
+    serialised by the caller, since they share the library's fixed scratch)."""
+    carr = cams if isinstance(cams, C.Array) else make_cameras(cams)
+    o = _opts(bg, gamma, max_steps=max_steps)
+    _check(lib().pot_render_noalloc(tree.handle, carr, len(carr), C.byref(o), _ptr(rgb), _ptr(t_final),
+                                    _stream(stream)))
+    return rgb
 
 
 def render_rays(tree: Tree, origins, dirs, rgb=None, t_final=None, bg=(0.0, 0.0, 0.0), gamma=0.0,

@@ -79,3 +79,18 @@ def test_noalloc_rejects_more_than_its_scratch_holds(env):
     st = fn(tree.handle, one, 1, None, C.c_void_p(host.ctypes.data), None,
             C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == pot.POT_ERR_INVALID_ARG
+
+
+def test_noalloc_python_wrapper(env):
+    pot, torch, _ = env
+    from paper_2103_14024_gb300 import synth as S
+    tree = pot.Tree.from_scene(S.scene_random(77, 5, 2, p_occ=0.3))
+    cams = S.make_cameras(S.orbit_c2ws(3, radius=3.0), 40, 24, 35.0)
+    ref, ref_tf = pot.render(tree, cams, gamma=1e-3, bg=(0.2, 0.1, 0.0), want_t_final=True)
+    rgb = torch.full_like(ref, -1.0)
+    tf = torch.full_like(ref_tf, -1.0)
+    out = pot.render_noalloc(tree, cams, rgb, t_final=tf, gamma=1e-3, bg=(0.2, 0.1, 0.0))
+    torch.cuda.synchronize()
+    assert out is rgb and torch.equal(rgb, ref) and torch.equal(tf, ref_tf)
+    pot.check()
+    tree.free()
