@@ -160,7 +160,10 @@ class RenderServer:
                 for r in batch:
                     r.t_launch = t
                 inflight.append((si, self.launcher(batch, streams[si]), batch))
-            if not (ready and free) and not (arrivals and arrivals[0].arrival <= self.clock() - t0):
+            # while launches are in flight, poll their events without sleeping (a
+            # sleep lasts tens of microseconds, which would add to every latency);
+            # sleep only when waiting for the next arrival
+            if not inflight and not (ready and free) and not (arrivals and arrivals[0].arrival <= self.clock() - t0):
                 time.sleep(2e-5)
         return requests
 
