@@ -39,6 +39,9 @@ NCU_TRAFFIC = {
     "f32": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 26.407e9},
     "f16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 8.974e9},
     "cb16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 4.800e9},
+    # bf16 0.6130 + 0.1087; the f32 tree without its cell index 1.5692 + 0.1122
+    "bf16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 9.021e9},
+    "f32-descent": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 21.017e9},
 }
 
 
