@@ -304,8 +304,11 @@ pot_status pot_camera_rays(const pot_camera *cams, int32_t n_cams, int64_t n, co
  * (256 B + 1024 camera records = 82,176 B per GPU, held until the process
  * exits) and makes no allocation at all.
  *   - Same arguments and results as pot_render, except: at most 1024 cameras
- *     per call (more gives POT_ERR_INVALID_ARG), and rgb / t_final must be
- *     device memory (nothing is staged); cams are in host memory.
+ *     per call (more gives POT_ERR_INVALID_ARG), and rgb / t_final (and
+ *     opts->seg_count / leaf_touched, when given) must be device memory
+ *     (nothing is staged; host arrays give POT_ERR_INVALID_ARG before any
+ *     launch); cams are in host memory and are copied to the array by every
+ *     call.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
  *     stream capture on the device.
@@ -367,6 +370,15 @@ typedef struct pot_render_item {
 } pot_render_item;
 
 pot_status pot_render_batch(const pot_render_item *items, int32_t n_items, pot_stream stream);
+
+/* ---------------------------------------------------------- measurement ---
+ * L2 read bandwidth of this GPU (the paper has no counterpart: a measurement
+ * kernel for the render path's L2 roofline).  Allocates a `bytes` device
+ * buffer (1 MiB .. 1 GiB; pick one that fits in L2, e.g. 32 MiB), fills it,
+ * reads it twice to make it L2-resident, then times `reps` (1..10000) full
+ * passes of 16-byte loads that bypass L1 (CUDA events on `stream`) and writes
+ * the bytes read per second / 1e9 to *gbs.  Synchronises; frees the buffer. */
+pot_status pot_probe_l2_read(int64_t bytes, int32_t reps, double *gbs, pot_stream stream);
 
 /* Number of CUDA kernels launched by this library in this process since it
  * was loaded (a counter for benchmarks). */

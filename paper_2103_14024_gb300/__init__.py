@@ -101,6 +101,7 @@ _SIGS = {
     "pot_visibility": [_p, _p, C.c_int32, _p, _p, _p],
     "pot_tree_prune": [_p, _p, C.c_float, _p, _p],
     "pot_tree_quantize": [_p, C.c_int32, _p, _p],
+    "pot_probe_l2_read": [C.c_int64, C.c_int32, _p, _p],
 }
 
 
@@ -138,6 +139,13 @@ def last_error() -> str:
 
 def launch_count() -> int:
     return int(lib().pot_launch_count())
+
+
+def probe_l2_read(nbytes: int = 32 << 20, reps: int = 200, stream=None) -> float:
+    """``pot_probe_l2_read``: L2 read bandwidth (GB/s) over an L2-resident buffer."""
+    out = C.c_double(0.0)
+    _check(lib().pot_probe_l2_read(int(nbytes), int(reps), C.byref(out), _stream(stream)))
+    return float(out.value)
 
 
 # ----------------------------------------------------------------------------

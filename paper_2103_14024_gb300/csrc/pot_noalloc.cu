@@ -121,6 +121,9 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
             return na_fail(POT_ERR_INVALID_ARG, "opts.flags must be 0 and max_steps >= 0");
         if ((opts->seg_count == nullptr) != (opts->leaf_touched == nullptr))
             return na_fail(POT_ERR_INVALID_ARG, "seg_count and leaf_touched go together");
+        // the kernel writes through these: host arrays are refused before any launch
+        if (opts->seg_count && (!on_device(opts->seg_count) || !on_device(opts->leaf_touched)))
+            return na_fail(POT_ERR_INVALID_ARG, "seg_count / leaf_touched must be device memory");
     }
     const int W = cams[0].width, H = cams[0].height;
     if (W <= 0 || H <= 0 || (int64_t)W * H > (1ll << 31)) return na_fail(POT_ERR_INVALID_ARG, "bad image size");

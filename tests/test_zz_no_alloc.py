@@ -81,6 +81,44 @@ def test_noalloc_rejects_more_than_its_scratch_holds(env):
     assert st == pot.POT_ERR_INVALID_ARG
 
 
+def test_noalloc_refuses_host_count_arrays(env):
+    """The counting outputs are written by the kernel, so host arrays are refused
+    before any launch, as pot_render refuses them."""
+    pot, torch, fn = env
+    from paper_2103_14024_gb300 import synth as S
+    tree = pot.Tree.from_scene(S.scene_tiny())
+    one = pot.make_cameras(S.cameras_tiny("generic"))
+    rgb = torch.empty((1, 64, 64, 3), dtype=torch.float32, device="cuda")
+    seg_h = np.zeros((1, 64, 64), np.int32)
+    touched_h = np.zeros(tree.info()["n_leaves"], np.uint8)
+    seg_d = torch.zeros((1, 64, 64), dtype=torch.int32, device="cuda")
+    touched_d = torch.zeros(tree.info()["n_leaves"], dtype=torch.uint8, device="cuda")
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for seg, touched in ((seg_h.ctypes.data, touched_d.data_ptr()), (seg_d.data_ptr(), touched_h.ctypes.data),
+                         (seg_h.ctypes.data, touched_h.ctypes.data)):
+        opts = pot._opts((0.0, 0.0, 0.0), 0.0)
+        opts.seg_count = seg
+        opts.leaf_touched = touched
+        st = fn(tree.handle, one, 1, C.byref(opts), C.c_void_p(rgb.data_ptr()), None, stream)
+        assert st == pot.POT_ERR_INVALID_ARG
+        assert "device memory" in pot.last_error()
+    torch.cuda.synchronize()
+    assert not seg_h.any() and not touched_h.any()
+    # device arrays are accepted and give pot_render's counts
+    opts = pot._opts((0.0, 0.0, 0.0), 0.0)
+    opts.seg_count = seg_d.data_ptr()
+    opts.leaf_touched = touched_d.data_ptr()
+    st = fn(tree.handle, one, 1, C.byref(opts), C.c_void_p(rgb.data_ptr()), None, stream)
+    assert st == pot.POT_OK, pot.last_error()
+    seg_r = torch.zeros_like(seg_d)
+    touched_r = torch.zeros_like(touched_d)
+    pot.render(tree, S.cameras_tiny("generic"), seg_count=seg_r, leaf_touched=touched_r)
+    torch.cuda.synchronize()
+    assert torch.equal(seg_d, seg_r) and torch.equal(touched_d, touched_r)
+    pot.check()
+    tree.free()
+
+
 def test_noalloc_python_wrapper(env):
     pot, torch, _ = env
     from paper_2103_14024_gb300 import synth as S
