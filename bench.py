@@ -31,17 +31,13 @@ METRIC = "Mrays/s @800^2 SH-3 (200 views, depth-9 octree, gamma 1e-4)"
 UNIT = "Mrays/s"
 N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 
-# DRAM bytes per render launch from the committed ncu capture (see
-# profiles/); reported only while the kernel sources still hash to ``sha``.
-NCU_TRAFFIC = {
-    # 16-view captures (one view group) x 12.5 = the 200-view launch:
-    # f32 1.9951 GB read + 0.1175 GB written; fp16 0.6095 + 0.1084; codebook 0.2839 + 0.1001
-    "f32": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 26.407e9},
-    "f16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 8.974e9},
-    "cb16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 4.800e9},
-    # bf16 0.6130 + 0.1087; the f32 tree without its cell index 1.5692 + 0.1122
-    "bf16": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 9.021e9},
-    "f32-descent": {"sha": "56a1d2cd53a9ec2f", "bytes_per_launch": 21.017e9},
+# Per-launch counters of the render kernel from the committed ncu captures
+# (profiles/render_kernel_main_units.md): one 16-view group of the benchmark
+# launch (the 200-view launch renders 12.5 such groups, and every counter
+# grows with the groups rendered).  Used only while the kernel sources still
+# hash to ``sha``; a changed kernel reports null until it is captured again.
+NCU_VIEWS = 16
+NCU_PROFILE = {
 }
 
 
@@ -72,8 +68,22 @@ def max_over_ranks(torch, dist, value: float, device) -> float:
 
 
 def job_value(world: int, rays_per_rank_step: int, wall_max: float, steps: int) -> float:
-    """Whole-job Mrays/s: the rays all ranks rendered per step / the slowest rank's step time."""
+    """Whole-job Mrays/s when every rank renders the same number of rays per step:
+    the rays all ranks rendered per step / the slowest rank's step time."""
     return world * rays_per_rank_step / (wall_max / steps) / 1e6
+
+
+def view_slice(rank: int, world: int, n_views: int):
+    """Views [start, end) that ``rank`` renders when the cameras are partitioned:
+    contiguous, balanced (sizes differ by at most one), disjoint, covering all
+    views; contiguous so that a rank's neighbouring views share leaves in L2."""
+    return n_views * rank // world, n_views * (rank + 1) // world
+
+
+def job_rays_per_step(partition: str, world: int, n_views: int, rays_per_view: int) -> int:
+    """Rays the whole job renders per step: each ray once when the views are
+    partitioned, once per rank when every rank renders all of them."""
+    return n_views * rays_per_view * (world if partition == "replicate" else 1)
 
 
 def dist_env():
@@ -190,7 +200,8 @@ def reference_arm(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak" if args.partition == "replicate" else "strong",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(scene, "f32"),
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -228,21 +239,43 @@ def algorithmic_bytes(pot, torch, tree, cams, dtype, leaf_bytes):
             "touched_bytes": segs * leaf_bytes + out_bytes, "rays": rays, "hit_rays": hits}
 
 
-def l2_read_peak(torch):
-    """Rough L2 bandwidth: repeated copy of a 24 MB buffer (read + write bytes)."""
-    x = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device="cuda").uniform_()
-    y = torch.empty_like(x)
-    for _ in range(20):
-        y.copy_(x)
-    torch.cuda.synchronize()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n = 400
-    s.record()
-    for _ in range(n):
-        y.copy_(x)
-    e.record()
-    torch.cuda.synchronize()
-    return 2 * x.numel() * 4 * n / (s.elapsed_time(e) * 1e-3) / 1e9
+KERNEL_TYPE = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "cb16": "cb16"}
+ISSUE_SLOTS_PER_SM_CYCLE = 4      # one warp instruction per cycle from each of an SM's 4 schedulers
+
+
+def measured_units(variant, sha, launch_ms, n_views, sm_mhz, l2_peak, hbm_peak):
+    """Each hardware unit's share of its peak for the render launch just timed,
+    from the committed ncu counters of this kernel version (scaled from the
+    captured 16 views to ``n_views``) over the CUDA-event launch time: DRAM
+    bytes (against the HBM copy peak), L2 bytes (against the library's own L2
+    read probe), warp instructions issued (against 4 per SM per cycle at the
+    clock sampled during the run), and the L1 data pipe's wavefronts (ncu's own
+    fraction of peak).  None when this kernel version has not been captured."""
+    prof = NCU_PROFILE.get(variant)
+    if not prof or prof.get("sha") != sha:
+        return None
+    scale = n_views / NCU_VIEWS
+    t = launch_ms * 1e-3
+    sms = 152
+    out = {"source": f"ncu, {NCU_VIEWS}-view capture x {scale:g} (profiles/render_kernel_main_units.md)"}
+    dram = (prof["dram_read"] + prof["dram_write"]) * scale
+    out["dram"] = {"bytes_per_launch": round(dram), "achieved_gbs": round(dram / t / 1e9, 1), "peak_gbs": hbm_peak,
+                   "frac": round(dram / t / 1e9 / hbm_peak, 4)}
+    if l2_peak:
+        l2 = prof["lts_bytes"] * scale
+        out["l2"] = {"bytes_per_launch": round(l2), "achieved_gbs": round(l2 / t / 1e9, 1),
+                     "peak_gbs": round(l2_peak, 1), "peak_source": "pot_probe_l2_read, 32 MiB, measured here",
+                     "frac": round(l2 / t / 1e9 / l2_peak, 4)}
+    inst = prof["warp_inst"] * scale
+    if sm_mhz:
+        peak_i = sms * ISSUE_SLOTS_PER_SM_CYCLE * sm_mhz * 1e6
+        out["issue"] = {"warp_inst_per_launch": round(inst), "achieved_ginst_s": round(inst / t / 1e9, 1),
+                        "peak_ginst_s": round(peak_i / 1e9, 1), "frac": round(inst / t / peak_i, 4)}
+    out["l1_data_pipe"] = {"wavefronts_per_launch": round(prof["l1_wavefronts"] * scale),
+                           "frac": round(prof["l1_pct"] / 100.0, 4), "frac_source": "ncu pct_of_peak (capture)"}
+    fr = {k: v["frac"] for k, v in out.items() if isinstance(v, dict) and "frac" in v}
+    out["binding"] = max(fr, key=fr.get)
+    return out
 
 
 def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
@@ -251,10 +284,21 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
     training views of 800x800 on the upper hemisphere; batches of random rays,
     MSE, backward, optimiser step.  Reports the backward kernel alone and the
     whole step in Mrays/s."""
-    cams = synth.cameras_train(n=100)
+    cams = synth.cameras_train(n=args.train_views)
     all_o, all_d = pot.camera_rays(cams)
     target = pot.render_rays(target_tree, all_o, all_d, gamma=GAMMA, near=2.0, far=6.0)
     tree = pot.Tree.from_scene(synth.perturbed(scene, 1003))
+    # held-out views (other hemisphere cameras) for the fit's PSNR against the target tree
+    held = synth.cameras_train(seed=1005, n=args.train_eval_views)
+    held_target = pot.render(target_tree, held, gamma=GAMMA)
+
+    def held_psnr():
+        mse = float(((pot.render(tree, held, gamma=GAMMA) - held_target) ** 2).mean().item())
+        return round(10.0 * math.log10(1.0 / mse), 3) if mse > 0 else float("inf")
+
+    psnr0 = held_psnr()
+    n_tiles_total = len(cams) * (W // 4) * (H // 8)
+    lane = torch.arange(32, device="cuda")
     info = tree.info()
     L, K = info["n_leaves"], info["sh_dim"]
     opt = pot.LeafOptimizer(tree, args.train_opt, lr_sigma=args.train_lr_sigma, lr_sh=args.train_lr_sh)
@@ -269,9 +313,17 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
     n_total = args.train_steps + 3
     for it in range(n_total):
         ev[0].record()
-        idx = torch.randint(0, all_o.shape[0], (B,), device="cuda", generator=gen)
-        if args.train_sort:   # same random rays, in view / row / column order: coherent warps
-            idx = torch.sort(idx).values
+        if args.train_batch_mode == "tiles":
+            # B / 32 random 4 x 8 pixel tiles of the training views, one tile per warp
+            tl = torch.randint(0, n_tiles_total, (B // 32,), device="cuda", generator=gen)
+            view, rem = tl // ((W // 4) * (H // 8)), tl % ((W // 4) * (H // 8))
+            px = (rem % (W // 4))[:, None] * 4 + lane % 4
+            py = (rem // (W // 4))[:, None] * 8 + lane // 4
+            idx = ((view[:, None] * H + py) * W + px).reshape(-1)
+        else:
+            idx = torch.randint(0, all_o.shape[0], (B,), device="cuda", generator=gen)
+            if args.train_sort:   # same random rays, in view / row / column order: coherent warps
+                idx = torch.sort(idx).values
         o, d, y = all_o[idx], all_d[idx], target[idx]
         ev[1].record()
         if args.train_fused:   # render + MSE + backward in one launch
@@ -302,23 +354,31 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
                 t_parts[name].append(ev[k].elapsed_time(ev[k + 1]))
     t_bwd = t_parts["backward"]
     t_step = [sum(v) for v in zip(*t_parts.values())]
+    psnr1 = held_psnr()
     pot.check()
     tree.free()
     mb, ms = sum(t_bwd) / len(t_bwd), sum(t_step) / len(t_step)
-    return {"workload": "fit a perturbed main tree to 100 training views of 800x800 (hemisphere), MSE",
+    return {"workload": f"fit a perturbed main tree to {args.train_views} training views of 800x800 (hemisphere), MSE",
             "rays_per_batch": B, "optimizer": args.train_opt, "lr_sigma": args.train_lr_sigma,
             "lr_sh": args.train_lr_sh, "steps": args.train_steps,
             "bwd_mrays_s": round(B / (mb * 1e-3) / 1e6, 2), "bwd_ms": round(mb, 4),
             "bwd_launch": ("pot_render_mse_backward: colour walk + MSE + gradient walk" if args.train_fused
                            else "pot_render_backward with the forward colour given"),
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
+            "batch": (f"{B // 32} random 4x8-pixel tiles of the training views, one per warp"
+                      if args.train_batch_mode == "tiles" else
+                      f"{B} random pixels of the training views" + (", sorted by view and pixel"
+                                                                    if args.train_sort else "")),
             "step_parts": ("random batch" + (" sorted by pixel" if args.train_sort else "") +
                            " + gather (torch), " +
                            ("zero grads (torch), fused forward + MSE + backward (one launch), "
                             if args.train_fused else "forward, MSE, zero grads (torch), backward, ") +
                            "optimiser step"),
             "parts_ms": {k: round(sum(v) / len(v), 4) for k, v in t_parts.items()},
-            "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6)}
+            "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6),
+            "heldout_psnr_db": {"before": psnr0, "after": psnr1,
+                                "views": f"{args.train_eval_views} held-out hemisphere views of 800x800 against "
+                                         "the target tree's renders"}}
 
 
 def serve_measure(pot, torch, synth, args):
@@ -349,12 +409,13 @@ def serve_measure(pot, torch, synth, args):
         for mode in ("batch", "alone"):
             reqs = [Request(i, float(arr[i]), int(tree_idx[i]), cams[i]) for i in range(len(cams))]
             srv = RenderServer(trees, budget, streams=3, gamma=GAMMA)
-            t0 = time.perf_counter()
-            srv.run(reqs, mode=mode)
+            torch.cuda.synchronize()
+            base = torch.cuda.memory_allocated()
+            torch.cuda.reset_peak_memory_stats()
+            srv.run(reqs, mode=mode, on_done=lambda r: None)   # each image consumed (dropped) when done
             torch.cuda.synchronize()
             out[f"{label}_{mode}"] = summarize(reqs)
-            for r in reqs:
-                r.rgb = None
+            out[f"{label}_{mode}"]["peak_output_bytes"] = int(torch.cuda.max_memory_allocated() - base)
     pot.check()
     for t in trees:
         t.free()
@@ -393,10 +454,13 @@ def main():
     ap.add_argument("--variants", default="f16,bf16,cb16,f32-descent",
                     help="extra leaf dtypes to time ('' for none); '<dtype>-descent' = that tree without its "
                          "cell index (cells located by descending the child array)")
+    ap.add_argument("--partition", default="views", choices=["views", "replicate"],
+                    help="N > 1: split the views across the ranks (each ray once, strong scaling) or let "
+                         "every rank render all of them (weak scaling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=30)
+    ap.add_argument("--train-steps", type=int, default=200)
     ap.add_argument("--train-batch", type=int, default=1 << 18)
     ap.add_argument("--train-sort", type=int, default=1,
                     help="1: order each random ray batch by view and pixel before rendering (the sum of the "
@@ -404,6 +468,12 @@ def main():
     ap.add_argument("--train-fused", type=int, default=0,
                     help="1: pot_render_mse_backward (render, loss and gradients in one launch); "
                          "0: pot_render_rays + pot_loss_mse + pot_render_backward")
+    ap.add_argument("--train-views", type=int, default=100,
+                    help="training views the ray batches are drawn from (100 in the benchmark; fewer for "
+                         "profiler captures)")
+    ap.add_argument("--train-eval-views", type=int, default=8, help="held-out views for the fit's PSNR")
+    ap.add_argument("--train-batch-mode", default="rays", choices=["rays", "tiles"],
+                    help="rays: random pixels; tiles: random 4x8-pixel tiles (32 neighbouring rays per warp)")
     ap.add_argument("--train-opt", default="rmsprop", choices=["sgd", "rmsprop", "adam"])
     ap.add_argument("--train-lr-sigma", type=float, default=1.0)
     ap.add_argument("--train-lr-sh", type=float, default=1e-2)
@@ -438,9 +508,19 @@ def main():
             dist.barrier()
 
     scene = synth.scene_shapes()
-    cams = synth.cameras_main(N_VIEWS, W, H)[:args.views]
+    all_cams = synth.cameras_main(N_VIEWS, W, H)[:args.views]
+    # N > 1: each rank renders a contiguous slice of the views (strong scaling,
+    # every ray once) or, with --partition replicate, all of them (weak scaling);
+    # no exchange on the data path either way
+    if args.partition == "views" and world > 1:
+        v0, v1 = view_slice(rank, world, len(all_cams))
+    else:
+        v0, v1 = 0, len(all_cams)
+    cams = all_cams[v0:v1]
     ccams = pot.make_cameras(cams)
     rays = len(cams) * W * H
+    job_rays = job_rays_per_step(args.partition, world, len(all_cams), W * H)
+    scaling = "weak" if args.partition == "replicate" else "strong"
 
     def measure(variant, e2e=False):
         dtype, _, mode = variant.partition("-")
@@ -482,52 +562,58 @@ def main():
     leaf_bytes = int(main_res["info"]["leaf_bytes"])
     alg = algorithmic_bytes(pot, torch, main_res["tree"], cams, args.dtype, leaf_bytes)
 
-    # whole-job time: max over ranks of the timed region; every rank rendered
-    # its own copy of the workload (weak scaling, no exchange on the data path)
+    # whole-job time: max over ranks of the timed region; value = the rays all
+    # ranks rendered per step / that time
     wall = max_over_ranks(torch, dist, main_res["wall"], "cuda")
     ms_per_step = 1e3 * wall / args.steps
-    value = job_value(world, rays, wall, args.steps)
+    value = job_rays / (wall / args.steps) / 1e6
     avg_launch_ms = sum(main_res["per"]) / len(main_res["per"])
     peak, peak_kind = measured_peaks()
     achieved = alg["hbm_bytes"] / (avg_launch_ms * 1e-3) / 1e9
     sha = kernel_sha()
-    traffic = None
-    if NCU_TRAFFIC.get(args.dtype, {}).get("sha") == sha:
-        traffic = NCU_TRAFFIC[args.dtype]["bytes_per_launch"]
+    l2_peak = None
+    if rank == 0:
+        try:
+            l2_peak = pot.probe_l2_read(32 << 20, 200)
+        except Exception:  # noqa: BLE001
+            l2_peak = None
+    units = measured_units(args.dtype, sha, avg_launch_ms, len(cams), main_res["clk"].get("sm_mhz"), l2_peak, peak)
+    traffic = units["dram"]["bytes_per_launch"] if units else None
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
         "ms_per_step_median": round(sorted(main_res["per"])[len(main_res["per"]) // 2], 3),
-        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-        "config": dict(workload_config(scene, args.dtype, len(cams)),
-                       cell_index_bytes=int(main_res["info"]["index_bytes"])),
+        "scaling": scaling, "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": dict(workload_config(scene, args.dtype, len(all_cams)),
+                       cell_index_bytes=int(main_res["info"]["index_bytes"]),
+                       partition=(f"views split across {world} ranks (rank 0: views {v0}..{v1 - 1})"
+                                  if args.partition == "views" and world > 1 else
+                                  f"every rank renders all {len(all_cams)} views" if world > 1 else "one GPU")),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "peak_source": f"hbm_gbs of {peak_kind}",
                      "algorithmic_bytes_per_launch": alg["hbm_bytes"],
-                     "kernel": "render_kernel<16,float,cams>", "avg_launch_ms": round(avg_launch_ms, 3)},
+                     "kernel": f"render_kernel<16,{KERNEL_TYPE[args.dtype]},cams>",
+                     "avg_launch_ms": round(avg_launch_ms, 3)},
         "gpu_launches": int(main_res["launches"]),
         "clocks": main_res["clk"],
     }
+    if units:
+        line["roofline"]["measured_units"] = units
+    line["roofline"]["touched_bytes_per_launch"] = alg["touched_bytes"]
     if rank == 0:
-        try:
-            l2p = l2_read_peak(torch)
-            line["l2"] = {"achieved": round(alg["touched_bytes"] / (avg_launch_ms * 1e-3) / 1e9, 1),
-                          "peak": round(l2p, 1), "unit": "GB/s", "peak_source": "24 MB device copy loop (measured here)",
-                          "touched_bytes_per_launch": alg["touched_bytes"],
-                          "frac": round(alg["touched_bytes"] / (avg_launch_ms * 1e-3) / 1e9 / l2p, 4)}
-        except Exception as e:  # noqa: BLE001
-            line["l2"] = {"error": str(e)}
         line["counts"] = {"unique_leaves_summed_over_views": alg["unique_leaves"],
                           "leaf_segments": alg["leaf_segments"],
                           "mean_leaf_segments_per_ray": round(alg["leaf_segments"] / rays, 3),
                           "hit_fraction": round(alg["hit_rays"] / rays, 4),
                           "mean_leaf_segments_per_hit_ray": round(alg["leaf_segments"] / max(1, alg["hit_rays"]), 3)}
     if not args.no_e2e:
-        e2e_value = world * rays / main_res["e2e_wall"] / 1e6
-        line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * len(cams),
-                       "d2h_bytes_per_step": 12 * rays}
+        e2e_wall = max_over_ranks(torch, dist, main_res["e2e_wall"], "cuda")
+        e2e_value = job_rays / e2e_wall / 1e6
+        n_job_views = job_rays // (W * H)
+        line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * n_job_views,
+                       "d2h_bytes_per_step": 12 * job_rays}
     variants = {}
     # per-GPU characteristics (other leaf types, training, serving) are measured at N = 1 only
     extras = world == 1
@@ -536,13 +622,14 @@ def main():
         w = r["wall"]
         vb = algorithmic_bytes(pot, torch, r["tree"], cams, vd.partition("-")[0], int(r["info"]["leaf_bytes"]))
         avg = sum(r["per"]) / len(r["per"])
-        variants[vd] = {"value": round(world * rays / (w / args.steps) / 1e6, 3),
+        vunits = measured_units(vd, sha, avg, len(cams), r["clk"].get("sm_mhz"), l2_peak, peak)
+        variants[vd] = {"value": round(rays / (w / args.steps) / 1e6, 3),
                         "ms_per_step": round(1e3 * w / args.steps, 3),
                         "roofline": {"bound": "hbm", "achieved": round(vb["hbm_bytes"] / (avg * 1e-3) / 1e9, 1),
                                      "peak": peak, "unit": "GB/s",
                                      "frac": round(vb["hbm_bytes"] / (avg * 1e-3) / 1e9 / peak, 4),
-                                     "traffic": (NCU_TRAFFIC.get(vd, {}).get("bytes_per_launch")
-                                                 if NCU_TRAFFIC.get(vd, {}).get("sha") == sha else None)},
+                                     "traffic": (vunits["dram"]["bytes_per_launch"] if vunits else None),
+                                     "measured_units": vunits},
                         "clocks": r["clk"], "leaf_bytes": int(r["info"]["leaf_bytes"]),
                         "cell_index_bytes": int(r["info"]["index_bytes"])}
         r["tree"].free()

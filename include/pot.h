@@ -86,7 +86,7 @@ typedef struct pot_tree pot_tree;
 
 typedef struct pot_build_desc {
     int32_t depth;         /* D, 1..12 (1..10 for pot_build from a dense grid) */
-    int32_t sh_degree;     /* 0..3 */
+    int32_t sh_degree;     /* 0..4 */
     int32_t leaf_dtype;    /* pot_dtype */
     float sigma_threshold; /* pot_build keeps voxel iff sigma > threshold */
     float bbox_lo[3];
@@ -203,7 +203,8 @@ pot_status pot_query(const pot_tree *tree, int64_t n, const float *xyz, int32_t 
                      pot_stream stream);
 
 /* Real SH basis Y_k, k < K, at the directions dirs [n][3] (normalised
- * inside) into Y [n][K] float32; device memory.  App. B.1. */
+ * inside) into Y [n][K] float32, K in {1, 4, 9, 16, 25}; device memory.
+ * App. B.1. */
 pot_status pot_sh_basis(int32_t K, int64_t n, const float *dirs, float *Y, pot_stream stream);
 
 /* --------------------------------------------------------------- render ---

@@ -208,8 +208,8 @@ pot_status check_desc(const pot_build_desc *d, int max_depth)
     if (!d) return fail(POT_ERR_INVALID_ARG, "desc is NULL");
     if (d->depth < 1 || d->depth > max_depth)
         return fail(POT_ERR_INVALID_ARG, "depth %d outside 1..%d", d->depth, max_depth);
-    if (d->sh_degree < 0 || d->sh_degree > 3)
-        return fail(POT_ERR_INVALID_ARG, "sh_degree %d outside 0..3", d->sh_degree);
+    if (d->sh_degree < 0 || d->sh_degree > 4)
+        return fail(POT_ERR_INVALID_ARG, "sh_degree %d outside 0..4", d->sh_degree);
     if (d->leaf_dtype < POT_F32 || d->leaf_dtype > POT_BF16)
         return fail(POT_ERR_INVALID_ARG, "leaf_dtype %d unknown", d->leaf_dtype);
     if (!(d->bbox_size > 0.f) || !std::isfinite(d->bbox_size))
@@ -675,7 +675,8 @@ pot_status pot_query(const pot_tree *t, int64_t n, const float *xyz, int32_t *le
 
 pot_status pot_sh_basis(int32_t K, int64_t n, const float *dirs, float *Y, pot_stream stream)
 {
-    if (K != 1 && K != 4 && K != 9 && K != 16) return fail(POT_ERR_INVALID_ARG, "K must be 1, 4, 9 or 16");
+    if (K != 1 && K != 4 && K != 9 && K != 16 && K != 25)
+        return fail(POT_ERR_INVALID_ARG, "K must be 1, 4, 9, 16 or 25");
     if (n < 0) return fail(POT_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return POT_OK;
     if (!dirs || !Y) return fail(POT_ERR_INVALID_ARG, "NULL array");

@@ -12,10 +12,22 @@
 // i.e. the paper's two passes: the composited colour C (the forward output,
 // or a first in-kernel pass) minus a running prefix.  Zero for sigma <= 0.
 // Gradients of L = sum_rays <dL/dC, C> are scattered with float reductions
-// (16-byte vector reductions where the row allows).
+// (16-byte vector reductions where the row allows).  With POT_BWD_AGG, lanes
+// of a warp that composite the same leaf in the same step first sum their
+// contributions with warp shuffles (warp-aggregated atomics) and one lane per
+// leaf issues the reductions.
 #include <cmath>
 
 #include "pot_render.cuh"
+
+#ifndef POT_BWD_AGG
+// warp-aggregated gradient scatter (lanes sharing a leaf reduce by shuffles
+// first).  Off: measured slower on 2^18-ray batches of the main tree, both for
+// random pixels (1.28 vs 0.86 ms) and for random 4 x 8 pixel tiles, whose
+// lanes do share leaves (0.75 vs 0.53 ms): the match and the 49-value shuffle
+// tree cost more than the float reductions they save.
+#define POT_BWD_AGG 0
+#endif
 
 namespace pot {
 
@@ -63,6 +75,48 @@ struct GradVisitor {
             gs = fmaf(g[c], fmaf(col, Tn, -(ctot[c] - prefix[c])), gs);
         }
         float *row = grad_sh + (int64_t)leaf * (3 * K);
+        float gsd = sraw > 0.f ? gs * delta : 0.f;  // zero for sigma <= 0 (same leaf: same sign)
+#if POT_BWD_AGG
+        // lanes compositing the same leaf: sum over the group with a shuffle
+        // tree over its members (ranked by lane); the lowest lane scatters
+        const unsigned act = __activemask();
+        const unsigned grp = __match_any_sync(act, leaf);
+        const unsigned shared_lanes = __ballot_sync(act, __popc(grp) > 1);
+        if (shared_lanes) {
+            const int lane = threadIdx.x & 31;
+            if (grp != (1u << lane)) {
+                const int n = __popc(grp);
+                const int rank = __popc(grp & ((1u << lane) - 1u));
+                const int nmax = (int)__reduce_max_sync(shared_lanes, (unsigned)n);
+                float v[3 * K];
+#pragma unroll
+                for (int j = 0; j < 3 * K; ++j) v[j] = gx[j % 3] * Y[j / 3];
+                for (int o = 1; o < nmax; o <<= 1) {
+                    const bool has = rank + o < n;
+                    const int src = has ? (int)__fns(grp, (unsigned)lane, o + 1) : lane;
+#pragma unroll
+                    for (int j = 0; j < 3 * K; ++j) {
+                        const float t = __shfl_sync(shared_lanes, v[j], src);
+                        if (has) v[j] += t;
+                    }
+                    const float t = __shfl_sync(shared_lanes, gsd, src);
+                    if (has) gsd += t;
+                }
+                if (rank == 0) {
+                    if ((3 * K) % 4 == 0) {
+#pragma unroll
+                        for (int j = 0; j < 3 * K; j += 4) red_add4(row + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 3 * K; ++j) red_add(row + j, v[j]);
+                    }
+                    if (sraw > 0.f) red_add(grad_sigma + leaf, gsd);
+                }
+                Tr = Tn;
+                return Tr < gamma;
+            }
+        }
+#endif
         if ((3 * K) % 4 == 0) {
 #pragma unroll
             for (int j = 0; j < 3 * K; j += 4)
@@ -72,7 +126,7 @@ struct GradVisitor {
 #pragma unroll
             for (int j = 0; j < 3 * K; ++j) red_add(row + j, gx[j % 3] * Y[j / 3]);
         }
-        if (sraw > 0.f) red_add(grad_sigma + leaf, gs * delta);
+        if (sraw > 0.f) red_add(grad_sigma + leaf, gsd);
         Tr = Tn;
         return Tr < gamma;
     }
@@ -178,6 +232,7 @@ cudaError_t launch_backward_t(const BackwardParams &bp, int K, int mode, cudaStr
     POT_PICK(4)
     POT_PICK(9)
     POT_PICK(16)
+    POT_PICK(25)
 #undef POT_PICK
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(bp.r.cells == nullptr);

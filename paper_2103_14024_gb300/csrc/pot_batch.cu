@@ -105,7 +105,7 @@ cudaError_t launch_batch_t(const BatchParams &bp, int K, bool need_stack, cudaSt
 {
     using Fn = void (*)(const BatchParams);
     Fn fn = K == 1 ? batch_kernel<1, T> : K == 4 ? batch_kernel<4, T> : K == 9 ? batch_kernel<9, T>
-          : K == 16 ? batch_kernel<16, T> : nullptr;
+          : K == 16 ? batch_kernel<16, T> : K == 25 ? batch_kernel<25, T> : nullptr;
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(need_stack);
     unsigned grid = 0;

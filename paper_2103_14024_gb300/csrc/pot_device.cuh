@@ -164,7 +164,7 @@ __device__ __forceinline__ int voxel_exact(float p, float lo, float h, float inv
 }
 
 // ------------------------------------------------------------------------
-// real spherical harmonics, degree <= 3 (App. B.1), polynomial form
+// real spherical harmonics, degree <= 4 (App. B.1), polynomial form
 // ------------------------------------------------------------------------
 constexpr double kPi = 3.14159265358979323846;
 
@@ -189,6 +189,15 @@ struct ShC {
     static constexpr float c3c = (float)(0.25 * csqrt(21.0 / (2.0 * kPi)));
     static constexpr float c3d = (float)(0.25 * csqrt(7.0 / kPi));
     static constexpr float c3e = (float)(0.25 * csqrt(105.0 / kPi));
+    // degree 4: sqrt(2) N_4^|m| times the leading factor of P_4^|m|, with
+    // (1 - z^2)^(|m|/2) cos / sin(|m| phi) written as Re / Im (x + i y)^|m|
+    static constexpr float c4a = (float)(0.75 * csqrt(35.0 / kPi));          // |m| = 4, sin
+    static constexpr float c4b = (float)(0.75 * csqrt(35.0 / (2.0 * kPi)));  // |m| = 3
+    static constexpr float c4c = (float)(0.75 * csqrt(5.0 / kPi));           // |m| = 2, sin
+    static constexpr float c4d = (float)(0.75 * csqrt(5.0 / (2.0 * kPi)));   // |m| = 1
+    static constexpr float c4e = (float)(0.1875 * csqrt(1.0 / kPi));         // m = 0
+    static constexpr float c4f = (float)(0.375 * csqrt(5.0 / kPi));          // |m| = 2, cos
+    static constexpr float c4g = (float)(0.1875 * csqrt(35.0 / kPi));        // |m| = 4, cos
 };
 
 template <int K>
@@ -215,6 +224,18 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
             Y[13] = ShC::c3c * x * (5.f * zz - 1.f);
             Y[14] = ShC::c3e * z * (xx - yy);
             Y[15] = ShC::c3a * x * (xx - 3.f * yy);
+            if (K > 16) {
+                const float z7 = 7.f * zz;
+                Y[16] = ShC::c4a * x * y * (xx - yy);
+                Y[17] = ShC::c4b * y * z * (3.f * xx - yy);
+                Y[18] = ShC::c4c * x * y * (z7 - 1.f);
+                Y[19] = ShC::c4d * y * z * (z7 - 3.f);
+                Y[20] = ShC::c4e * (zz * (35.f * zz - 30.f) + 3.f);
+                Y[21] = ShC::c4d * x * z * (z7 - 3.f);
+                Y[22] = ShC::c4f * (xx - yy) * (z7 - 1.f);
+                Y[23] = ShC::c4b * x * z * (xx - 3.f * yy);
+                Y[24] = ShC::c4g * (xx * (xx - 3.f * yy) - yy * (3.f * xx - yy));
+            }
         }
     }
 }

@@ -54,7 +54,7 @@ cudaError_t launch_visibility_t(const RenderParams &p, int K, float *max_w, cuda
 {
     using Fn = void (*)(const RenderParams, float *);
     Fn fn = K == 1 ? visibility_kernel<1, T> : K == 4 ? visibility_kernel<4, T> : K == 9 ? visibility_kernel<9, T>
-          : K == 16 ? visibility_kernel<16, T> : nullptr;
+          : K == 16 ? visibility_kernel<16, T> : K == 25 ? visibility_kernel<25, T> : nullptr;
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(p.cells == nullptr);
     unsigned grid = 0;

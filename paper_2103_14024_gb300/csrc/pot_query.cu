@@ -91,6 +91,7 @@ cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaS
     case 4: k_sh_basis<4><<<grid1(n), 256, 0, s>>>(n, dirs, Y); break;
     case 9: k_sh_basis<9><<<grid1(n), 256, 0, s>>>(n, dirs, Y); break;
     case 16: k_sh_basis<16><<<grid1(n), 256, 0, s>>>(n, dirs, Y); break;
+    case 25: k_sh_basis<25><<<grid1(n), 256, 0, s>>>(n, dirs, Y); break;
     default: return cudaErrorInvalidValue;
     }
     count_launch();

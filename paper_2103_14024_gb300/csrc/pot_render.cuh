@@ -431,6 +431,7 @@ cudaError_t launch_render_t(const RenderParams &p, int K, bool cams, bool count,
     POT_PICK(4)
     POT_PICK(9)
     POT_PICK(16)
+    POT_PICK(25)
 #undef POT_PICK
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(p.cells == nullptr);

@@ -7,6 +7,10 @@ packed, as they come, into ``pot_render_batch`` launches (one work list per
 launch, mixed trees and resolutions) on a small ring of CUDA streams, so work
 that arrives while earlier launches run overlaps with them on the device.
 Completion is read from CUDA events; a finished request releases its budget.
+Outputs of finished requests are handed to the caller (``on_done``); when
+the caller consumes them there, device memory held by outputs stays within
+the admission budget; without ``on_done`` the finished images stay on the
+requests, outside the budget, for the caller to keep or drop.
 Mode ``alone`` renders one request per launch on one stream, in arrival order
 (the baseline the batching is compared with).
 
@@ -101,8 +105,14 @@ class RenderServer:
         return ev
 
     # -- the loop -------------------------------------------------------------
-    def run(self, requests, mode: str = "batch"):
-        """Serves ``requests`` (sorted by arrival) in real time; returns the requests with timestamps."""
+    def run(self, requests, mode: str = "batch", on_done=None):
+        """Serves ``requests`` (sorted by arrival) in real time; returns the requests with timestamps.
+
+        ``on_done(request)`` is called as each request completes (its image in
+        ``request.rgb``); the server then drops its reference to the image, so
+        the bytes it returns to the budget are really free.  Without it,
+        completed images stay on the requests: they leave the budget at
+        completion and are the caller's to free."""
         assert mode in ("batch", "alone")
         n_streams = self.n_streams if mode == "batch" else 1
         per_launch = None if mode == "batch" else 1
@@ -141,6 +151,9 @@ class RenderServer:
                     t = self.clock() - t0
                     for r in reqs:
                         r.t_done = t
+                        if on_done is not None:
+                            on_done(r)
+                            r.rgb = None
                         self.adm.release(r.out_bytes)
                     free.append(si)
                 else:

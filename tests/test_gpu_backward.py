@@ -35,7 +35,7 @@ def _close(gpu, ref, name):
     assert err <= REL * scale, f"{name}: max err {err:.3e} vs scale {scale:.3e}"
 
 
-@pytest.mark.parametrize("seed,D,deg", [(51, 3, 0), (52, 4, 1), (53, 5, 2), (54, 5, 3), (55, 6, 3)])
+@pytest.mark.parametrize("seed,D,deg", [(51, 3, 0), (52, 4, 1), (53, 5, 2), (54, 5, 3), (55, 6, 3), (56, 5, 4)])
 @pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.3, 0.6, 0.9)])
 def test_backward_vs_oracle(pot, oracle_mod, torch_mod, seed, D, deg, bg):
     torch = torch_mod
@@ -60,6 +60,48 @@ def test_backward_vs_oracle(pot, oracle_mod, torch_mod, seed, D, deg, bg):
     _close(gs2.cpu().numpy(), rs, "grad_sigma (two-pass)")
     _close(gh2.cpu().numpy(), rh, "grad_sh (two-pass)")
     pot.check()
+
+
+@pytest.mark.parametrize("gamma", [0.0, 1e-4])
+def test_backward_vs_oracle_main_depth5(pot, oracle_mod, torch_mod, gamma):
+    """The optimisation benchmark's setting on a depth-5 copy of the main scene
+    (32^3 grid, SH degree 3): a perturbed copy (SH + N(0, 0.3), sigma x
+    U(0.5, 1.5)) seen through training cameras on the upper hemisphere (800 x
+    800, near 2, far 6), upstream gradient = the MSE gradient against the
+    target tree's colours; GPU gradients against the oracle's, 1e-4 x max.
+    With gamma > 0 a ray may stop one segment apart on the two sides, so only
+    rays whose segment counts agree (decided before either backward) are used."""
+    torch = torch_mod
+    target_sc = S.scene_shapes(depth=5, sh_degree=3)
+    sc = S.perturbed(target_sc, 1003)
+    cams = S.cameras_train(n=100)[::25]
+    o_all, d_all = oracle_mod.cam_rays(cams)
+    pick = np.random.default_rng(5).choice(o_all.shape[0], 30000, replace=False)
+    o, d = np.ascontiguousarray(o_all[pick]), np.ascontiguousarray(d_all[pick])
+    ot, ot_target = oracle_mod.build_sparse(sc), oracle_mod.build_sparse(target_sc)
+    fwd = oracle_mod.render_rays(ot, o, d, near=2.0, far=6.0, gamma=gamma)
+    target = oracle_mod.render_rays(ot_target, o, d, near=2.0, far=6.0, gamma=gamma)["rgb"]
+    t = pot.Tree.from_scene(sc)
+    og, od = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    seg = torch.zeros(o.shape[0], dtype=torch.int32, device="cuda")
+    touched = torch.zeros(t.info()["n_leaves"], dtype=torch.uint8, device="cuda")
+    pot.render_rays(t, og, od, gamma=gamma, near=2.0, far=6.0, seg_count=seg, leaf_touched=touched)
+    keep = seg.cpu().numpy() == fwd["n_seg"]
+    if gamma == 0.0:
+        assert keep.all()
+    assert keep.mean() > 0.99 and (fwd["n_seg"][keep] > 0).sum() > 5000
+    o, d = np.ascontiguousarray(o[keep]), np.ascontiguousarray(d[keep])
+    g = (2.0 / (3 * o.shape[0])) * (fwd["rgb"][keep] - target[keep])       # MSE gradient (oracle colours)
+    og, od = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    gg = torch.from_numpy(g.astype(np.float32)).cuda()
+    gs, gh = pot.render_backward(t, og, od, gg, gamma=gamma, near=2.0, far=6.0)
+    rs, rh = oracle_mod.backward_rays(ot, o, d, g.astype(np.float32).astype(np.float64), near=2.0, far=6.0,
+                                      gamma=gamma)
+    assert float(np.abs(rs).max()) > 0 and float(np.abs(rh).max()) > 0
+    _close(gs.cpu().numpy(), rs, "grad_sigma")
+    _close(gh.cpu().numpy(), rh, "grad_sh")
+    pot.check()
+    t.free()
 
 
 def test_backward_vs_gpu_finite_differences(pot, torch_mod):

@@ -25,7 +25,8 @@ def pot():
 
 
 @pytest.mark.parametrize("seed,D,deg,bits,dtype", [(81, 4, 1, 4, "f32"), (82, 5, 2, 6, "f32"),
-                                                    (83, 6, 3, 8, "f16"), (84, 3, 0, 16, "f32")])
+                                                    (83, 6, 3, 8, "f16"), (84, 3, 0, 16, "f32"),
+                                                    (85, 4, 4, 5, "f32")])
 def test_quantized_values_bitexact(pot, oracle_mod, seed, D, deg, bits, dtype):
     sc = S.scene_random(seed, D, deg, p_occ=0.4, sigma_mu=2.0)
     base = oracle_mod.build_sparse(sc, dtype=dtype)

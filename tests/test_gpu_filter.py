@@ -24,7 +24,8 @@ def pot():
     return P
 
 
-@pytest.mark.parametrize("seed,D,deg,dtype", [(71, 4, 1, "f32"), (72, 5, 2, "f32"), (73, 6, 3, "f16")])
+@pytest.mark.parametrize("seed,D,deg,dtype", [(71, 4, 1, "f32"), (72, 5, 2, "f32"), (73, 6, 3, "f16"),
+                                              (74, 5, 4, "bf16")])
 @pytest.mark.parametrize("gamma", [0.0, 0.02])
 def test_visibility_vs_oracle(pot, oracle_mod, seed, D, deg, dtype, gamma):
     sc = S.scene_random(seed, D, deg, p_occ=0.35, sigma_mu=2.0)

@@ -46,7 +46,7 @@ def _export_equal(pot, oracle_mod, sc, dtype="f32"):
 # ---------------------------------------------------------------- build ----
 
 @pytest.mark.parametrize("seed,D,deg", [(1, 1, 0), (2, 2, 1), (3, 3, 2), (4, 4, 3), (5, 5, 0), (6, 6, 3),
-                                        (7, 7, 1)])
+                                        (7, 7, 1), (8, 5, 4)])
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_build_bitexact(pot, oracle_mod, seed, D, deg, dtype):
     sc = S.scene_random(seed, D, deg, p_occ=0.3, sh_std=2.0)
@@ -140,7 +140,7 @@ def test_sh_basis_vs_oracle(pot, oracle_mod, torch_mod):
     rng = np.random.default_rng(3)
     d = rng.normal(size=(20000, 3)).astype(np.float32)
     d = np.concatenate([d, np.eye(3, dtype=np.float32), -np.eye(3, dtype=np.float32)])
-    for K in (1, 4, 9, 16):
+    for K in (1, 4, 9, 16, 25):
         Y = pot.sh_basis(K, torch_mod.from_numpy(d).cuda()).cpu().numpy()
         ref = oracle_mod.sh_basis(K, d.astype(np.float64))
         assert np.abs(Y - ref).max() <= 1e-6
@@ -178,7 +178,7 @@ def test_render_tiny(pot, oracle_mod, variant, gamma, bg):
 
 
 @pytest.mark.parametrize("seed,D,deg", [(31, 2, 0), (32, 3, 1), (33, 4, 2), (34, 5, 3), (35, 6, 3),
-                                        (36, 7, 2)])
+                                        (36, 7, 2), (37, 5, 4), (38, 6, 4)])
 @pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
 def test_render_random_trees_rays(pot, oracle_mod, torch_mod, seed, D, deg, dtype):
     sc = S.scene_random(seed, D, deg, p_occ=0.35, sigma_mu=2.0, sigma_s=1.5, sh_std=1.0)

@@ -17,7 +17,7 @@ def env():
     import paper_2103_14024_gb300 as pot
     pot.lib()
     specs = [(5, 1, "f16", 2001), (6, 2, "f16", 2002), (7, 3, "f16", 2003), (8, 3, "f16", 2004),
-             (6, 3, "f32", 2005), (5, 0, "bf16", 2006)]
+             (6, 3, "f32", 2005), (5, 0, "bf16", 2006), (5, 4, "f32", 2007)]
     scenes = [S.scene_shapes(seed, depth=D, sh_degree=deg) for D, deg, _, seed in specs]
     trees = [pot.Tree.from_scene(sc, dtype=dt) for sc, (_, _, dt, _) in zip(scenes, specs)]
     return pot, torch, trees, scenes, specs

@@ -201,3 +201,16 @@ def test_stored_values_rounded(oracle_mod):
         h_ref, _ = oracle_mod.round_values(sc.sh, dt)
         assert np.array_equal(sigma, s_ref.astype(np.float64))
         assert np.array_equal(sh, h_ref.astype(np.float64))
+
+
+@pytest.mark.parametrize("seed,depth,deg", [(1004, 5, 1), (1006, 6, 3), (1001, 7, 2)])
+def test_scene_generator_torch_form_equals_numpy_form(seed, depth, deg):
+    """The torch form of the shapes generator (used where the serving trees are
+    generated on the device) gives the numpy form's leaves bit for bit, so the
+    oracle may be given either."""
+    torch = pytest.importorskip("torch")
+    a = S.scene_shapes(seed, depth=depth, sh_degree=deg)
+    b = S.scene_shapes_torch(seed, depth=depth, sh_degree=deg, device="cpu")
+    assert np.array_equal(a.morton, b.morton.numpy().view(np.uint64))
+    assert np.array_equal(a.sigma.view(np.uint32), b.sigma.numpy().view(np.uint32))
+    assert np.array_equal(a.sh.view(np.uint32), b.sh.numpy().view(np.uint32))

@@ -116,3 +116,29 @@ def test_summary_breakdowns_are_consistent():
     for r in reqs:
         assert r.arrival <= r.t_admit <= r.t_launch <= r.t_done
     assert s["p50_wait_ms"] >= 0 and s["p50_run_ms"] > 0
+
+
+def test_on_done_hands_over_each_output_once_and_drops_it():
+    """With on_done, every finished output is handed over exactly once, after
+    completion, and the server keeps no reference to it afterwards: the bytes
+    returned to the budget are free."""
+    reqs = _requests(60, 5000.0)
+    clock = FakeClock()
+    live = set()
+    srv = RenderServer(trees=[None] * 4, hbm_budget_bytes=30_000_000, streams=3, clock=clock,
+                       launcher=lambda *a: None, allocator=lambda r: (live.add(r.rid), ("img", r.rid))[1],
+                       stream_factory=lambda n: [None] * n)
+    rec = Recorder(clock, srv)
+    srv.launcher = rec
+    seen = []
+
+    def on_done(r):
+        assert r.rgb == ("img", r.rid) and r.t_done >= r.t_launch >= r.t_admit >= r.arrival
+        seen.append(r.rid)
+        live.discard(r.rid)
+
+    srv.run(reqs, mode="batch", on_done=on_done)
+    done = [r.rid for r in reqs if not r.rejected]
+    assert sorted(seen) == sorted(done) and len(seen) == len(set(seen))
+    assert all(r.rgb is None for r in reqs) and not live
+    assert rec.max_used <= 30_000_000 and srv.adm.used == 0
