@@ -451,9 +451,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f16", "bf16", "cb16"])
-    ap.add_argument("--variants", default="f16,bf16,cb16,f32-descent",
+    ap.add_argument("--variants", default="f16,bf16,cb16,f32-descent,f32-brick,f16-brick",
                     help="extra leaf dtypes to time ('' for none); '<dtype>-descent' = that tree without its "
-                         "cell index (cells located by descending the child array)")
+                         "cell index (cells located by descending the child array); '<dtype>-brick' = with the "
+                         "brick layout of the cell index instead of the dense one")
     ap.add_argument("--partition", default="views", choices=["views", "replicate"],
                     help="N > 1: split the views across the ranks (each ray once, strong scaling) or let "
                          "every rank render all of them (weak scaling)")
@@ -532,6 +533,8 @@ def main():
             tree = pot.Tree.from_scene(scene, dtype=dtype)
         if mode == "descent":
             tree.set_cell_index(False)
+        elif mode == "brick":
+            tree.set_cell_index("brick")
         info = tree.info()
         rgb = torch.empty((len(cams), H, W, 3), dtype=torch.float32, device="cuda")
 
@@ -631,7 +634,8 @@ def main():
                                      "traffic": (vunits["dram"]["bytes_per_launch"] if vunits else None),
                                      "measured_units": vunits},
                         "clocks": r["clk"], "leaf_bytes": int(r["info"]["leaf_bytes"]),
-                        "cell_index_bytes": int(r["info"]["index_bytes"])}
+                        "cell_index_bytes": int(r["info"]["index_bytes"]),
+                        "cell_index": {0: "none", 2: "dense", 3: "brick"}[int(r["info"]["index_kind"])]}
         r["tree"].free()
     if variants:
         line["variants"] = variants

@@ -128,6 +128,7 @@ typedef struct pot_tree_info {
     int32_t device;
     int64_t index_bytes;  /* device bytes of the cell index (pot_tree_set_cell_index), 0 if none;
                              included in bytes */
+    int32_t index_kind;   /* pot_cells layout of the cell index */
 } pot_tree_info;
 
 /* ---------------------------------------------------------------- build ---
@@ -166,33 +167,51 @@ pot_status pot_tree_set_values(pot_tree *tree, const float *sigma, const float *
 pot_status pot_tree_free(pot_tree *tree);
 
 /* Cell index of a tree (the paper has no counterpart: an acceleration
- * structure of this library).  A dense int32 array over the 2^D grid that
- * gives, for every voxel, the leaf holding it (>= 0) -- what the descent of
- * the child array (Sec. 3.2 "Rendering") finds -- or, for an empty voxel, a
- * box of empty space around it that a ray crosses in one step:
+ * structure of this library).  It gives, for every voxel of the 2^D grid, the
+ * leaf holding it (>= 0) -- what the descent of the child array (Sec. 3.2
+ * "Rendering") finds -- or, for an empty voxel, a box of empty space around
+ * it that a ray crosses in one step:
  *   -(2 + 2 l)   the empty octree node of level l that contains it, or
  *   -(3 + 2 e)   the cube of (2e+1)^3 voxels centred on it (every voxel within
  *                Chebyshev distance e is empty; e <= 63), recorded where
  *                2e + 2 > 2^(D-l).
+ * Two layouts:
+ *   POT_CELLS_DENSE  one int32 entry per voxel: 4 * 8^D bytes (537 MB at
+ *                    D = 9, 4.3 GB at D = 10); D <= 10 (the build also needs
+ *                    2 * 8^D bytes of scratch); e is the voxel's own
+ *                    Chebyshev distance to the nearest leaf - 1.  A cell is
+ *                    one 4-byte load.
+ *   POT_CELLS_BRICK  one int32 per 4 x 4 x 4 brick of voxels (4 * 8^(D-2)
+ *                    bytes: 8 MB at D = 9, 67 MB at D = 10, 537 MB at
+ *                    D = 11) plus 64 entries (256 bytes) for each brick that
+ *                    holds a leaf; D in 3..11.  A brick without a leaf has
+ *                    one entry for all its voxels: the empty node around
+ *                    the brick, or the cube of half-extent 4 (b - 1) where b
+ *                    is the brick's Chebyshev distance, in bricks, to the
+ *                    nearest brick holding a leaf; inside a brick with a leaf
+ *                    empty voxels get their empty node.  A cell is two
+ *                    dependent 4-byte loads.
  * A leaf's segment is bounded by the crossing times of its own faces however
  * the empty space before it was stepped over, so renders, gradients and
- * visibility weights are bit-identical with and without the index; with it,
- * locating each cell is one 4-byte load instead of a descent and empty space
- * takes fewer steps.  Size 4 * 8^D bytes (537 MB at D = 9, 4.3 GB at
- * D = 10); only for D <= 10 (the build also needs 2 * 8^D bytes of scratch).
- *   Every tree of depth <= 10 that pot_build, pot_build_sparse,
- *   pot_tree_prune or pot_tree_quantize creates gets one when the device has
- *   room for it (pot_tree_info.index_bytes says whether it has).
- *   enable = 1 builds it if absent (POT_ERR_UNSUPPORTED for D > 10,
- *   POT_ERR_OOM when the device is full); enable = 0 synchronises the device
- *   and frees it.  The tree's structure is never changed after creation, so
- *   the index stays valid under pot_tree_set_values and pot_step.
- *   Not thread-safe against renders of the same tree from other host threads. */
+ * visibility weights are bit-identical with either index and without one.
+ *   Every tree that pot_build, pot_build_sparse, pot_tree_prune or
+ *   pot_tree_quantize creates gets the default layout for its depth (dense
+ *   for D <= 9, brick for 10 <= D <= 11) when the device has room for it
+ *   (pot_tree_info.index_bytes / index_kind say which it has).
+ *   enable = 0 synchronises the device and frees it; 1 builds the default
+ *   layout, 2 the dense, 3 the brick layout (replacing another layout;
+ *   POT_ERR_UNSUPPORTED outside the layout's depths, POT_ERR_OOM when the
+ *   device is full).  The tree's structure is never changed after
+ *   creation, so the index stays valid under pot_tree_set_values and
+ *   pot_step.  Not thread-safe against renders of the same tree from other
+ *   host threads. */
+typedef enum pot_cells { POT_CELLS_NONE = 0, POT_CELLS_DENSE = 2, POT_CELLS_BRICK = 3 } pot_cells;
 pot_status pot_tree_set_cell_index(pot_tree *tree, int32_t enable, pot_stream stream);
 
-/* The cell index (entries as above) as a dense [R][R][R] int32 array indexed
- * [x][y][z] (R = 2^D) into caller memory (host or device);
- * POT_ERR_INVALID_ARG if the tree has none.  (No counterpart in the paper.) */
+/* The cell index (entries as above, each voxel's own entry in either layout)
+ * as a dense [R][R][R] int32 array indexed [x][y][z] (R = 2^D) into caller
+ * memory (host or device); POT_ERR_INVALID_ARG if the tree has none.  (No
+ * counterpart in the paper.) */
 pot_status pot_tree_export_cell_index(const pot_tree *tree, int32_t *out, pot_stream stream);
 
 /* ---------------------------------------------------------------- query ---

@@ -68,7 +68,10 @@ class TreeInfo(C.Structure):
                 ("leaf_dtype", C.c_int32), ("n_nodes", C.c_int64), ("n_leaves", C.c_int64),
                 ("bytes", C.c_int64), ("leaf_bytes", C.c_int64), ("bbox_lo", C.c_float * 3),
                 ("bbox_size", C.c_float), ("saturated", C.c_int32), ("device", C.c_int32),
-                ("index_bytes", C.c_int64)]
+                ("index_bytes", C.c_int64), ("index_kind", C.c_int32)]
+
+
+CELLS = {"none": 0, "default": 1, "dense": 2, "brick": 3}
 
 
 assert C.sizeof(Camera) == 80
@@ -285,10 +288,13 @@ class Tree:
                                      _stream(stream)))
         return child, sigma, sh, morton
 
-    def set_cell_index(self, enable: bool = True, stream=None):
-        """``pot_tree_set_cell_index``: build (True) or free (False) the per-voxel cell index
-        that replaces the child-array descent when locating cells (depth <= 10)."""
-        _check(lib().pot_tree_set_cell_index(self.handle, 1 if enable else 0, _stream(stream)))
+    def set_cell_index(self, enable=True, stream=None):
+        """``pot_tree_set_cell_index``: free (False / "none") the cell index that replaces the
+        child-array descent when locating cells, or build it: True / "default" (the layout for
+        the tree's depth), "dense" (one entry per voxel, depth <= 10) or "brick" (one entry per
+        4^3 brick plus the entries of bricks holding a leaf, depth 3..11)."""
+        mode = CELLS[enable] if isinstance(enable, str) else (1 if enable else 0)
+        _check(lib().pot_tree_set_cell_index(self.handle, mode, _stream(stream)))
 
     def export_cell_index(self, device=None, stream=None):
         """``pot_tree_export_cell_index``: int32 [R, R, R] indexed [x][y][z]: leaf index; for an

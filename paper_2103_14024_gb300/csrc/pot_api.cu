@@ -243,23 +243,34 @@ void destroy_tree(pot_tree *t)
     cudaFree(t->sh);
     cudaFree(t->morton);
     cudaFree(t->codebook);
-    cudaFree(t->cells);
+    free_cell_index(t);
     delete t;
 }
 
-// Gives a new tree of depth <= kCellIndexMaxDepth its cell index.  A device
-// too full for it leaves the tree without one (cells are then found by
-// descending the child array); any other failure is returned.
+// Cell index layout a tree of depth D gets by default: dense up to depth 9
+// (537 MB at D = 9; one load per cell), bricks for depths 10 and 11 (the
+// dense layout would take 4.3 GB at D = 10 and cannot be built beyond).
+int default_cell_kind(int D)
+{
+    if (D <= kDenseDefaultMaxDepth) return POT_CELLS_DENSE;
+    if (D >= kBrickIndexMinDepth && D <= kBrickIndexMaxDepth) return POT_CELLS_BRICK;
+    return POT_CELLS_NONE;
+}
+
+// Gives a new tree its default cell index.  A device too full for it leaves
+// the tree without one (cells are then found by descending the child array);
+// any other failure is returned.
 cudaError_t attach_cell_index(pot_tree *t, cudaStream_t s)
 {
-    if (t->desc.depth > kCellIndexMaxDepth) return cudaSuccess;
-    cudaError_t e = build_cell_index(t, s);
+    const int kind = default_cell_kind(t->desc.depth);
+    if (kind == POT_CELLS_NONE) return cudaSuccess;
+    cudaError_t e = build_cell_index(t, kind, s);
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
         return cudaSuccess;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) t->bytes += cell_index_entries(t->desc.depth) * 4;
+    if (e == cudaSuccess) t->bytes += t->index_bytes;
     return e;
 }
 
@@ -328,6 +339,7 @@ void fill_tree_params(RenderParams &p, const pot_tree *t, const pot_render_opts 
     std::memset(&p, 0, sizeof(p));
     p.child = t->child;
     p.cells = t->cells;
+    p.btab = t->btab;
     p.sigma = t->sigma;
     p.sh = t->sh;
     p.codebook = t->codebook;
@@ -549,7 +561,8 @@ pot_status pot_tree_get_info(const pot_tree *t, pot_tree_info *info)
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = t->desc.bbox_lo[a];
     info->bbox_size = t->desc.bbox_size;
     info->saturated = t->saturated;
-    info->index_bytes = t->cells ? cell_index_entries(t->desc.depth) * 4 : 0;
+    info->index_bytes = t->index_bytes;
+    info->index_kind = t->cell_kind;
     info->device = t->device;
     return POT_OK;
 }
@@ -625,31 +638,33 @@ pot_status pot_tree_export_cell_index(const pot_tree *t, int32_t *out, pot_strea
 pot_status pot_tree_set_cell_index(pot_tree *t, int32_t enable, pot_stream stream)
 {
     if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
-    if (enable != 0 && enable != 1) return fail(POT_ERR_INVALID_ARG, "enable must be 0 or 1");
+    if (enable < 0 || enable > 3) return fail(POT_ERR_INVALID_ARG, "enable must be 0, 1, 2 or 3");
     DeviceGuard g(t->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t bytes = cell_index_entries(t->desc.depth) * 4;
-    if (!enable) {
-        if (t->cells) {
-            POT_CUDA(cudaDeviceSynchronize(), "sync");
-            POT_CUDA(cudaFree(t->cells), "free cell index");
-            t->cells = nullptr;
-            t->bytes -= bytes;
-        }
-        return POT_OK;
+    const int D = t->desc.depth;
+    const int kind = enable == 1 ? default_cell_kind(D) : enable;
+    if (enable == 1 && kind == POT_CELLS_NONE)
+        return fail(POT_ERR_UNSUPPORTED, "no cell index for depth %d", D);
+    if (kind == t->cell_kind) return POT_OK;
+    if (kind == POT_CELLS_DENSE && D > kCellIndexMaxDepth)
+        return fail(POT_ERR_UNSUPPORTED, "no dense cell index for depth %d (at most %d)", D, kCellIndexMaxDepth);
+    if (kind == POT_CELLS_BRICK && (D < kBrickIndexMinDepth || D > kBrickIndexMaxDepth))
+        return fail(POT_ERR_UNSUPPORTED, "no brick cell index for depth %d (%d..%d)", D, kBrickIndexMinDepth,
+                    kBrickIndexMaxDepth);
+    if (t->cell_kind != POT_CELLS_NONE) {
+        POT_CUDA(cudaDeviceSynchronize(), "sync");
+        t->bytes -= t->index_bytes;
+        free_cell_index(t);
     }
-    if (t->cells) return POT_OK;
-    if (t->desc.depth > kCellIndexMaxDepth)
-        return fail(POT_ERR_UNSUPPORTED, "no cell index for depth %d (at most %d)", t->desc.depth,
-                    kCellIndexMaxDepth);
-    cudaError_t e = build_cell_index(t, s);
+    if (kind == POT_CELLS_NONE) return POT_OK;
+    cudaError_t e = build_cell_index(t, kind, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaErrorMemoryAllocation) {
         (void)cudaGetLastError();
-        return fail(POT_ERR_OOM, "cell index: %lld bytes", (long long)bytes);
+        return fail(POT_ERR_OOM, "cell index: device full");
     }
     POT_CUDA(e, "cell index");
-    t->bytes += bytes;
+    t->bytes += t->index_bytes;
     return POT_OK;
 }
 
@@ -882,6 +897,10 @@ pot_status pot_tree_quantize(const pot_tree *t, int32_t bits, pot_tree **out, po
     q->morton = nullptr;
     q->codebook = nullptr;
     q->cells = nullptr;
+    q->btab = nullptr;
+    q->n_bricks = 0;
+    q->cell_kind = POT_CELLS_NONE;
+    q->index_bytes = 0;
     cudaError_t e = cudaMalloc(&q->child, sizeof(int32_t) * 8 * t->n_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&q->morton, sizeof(uint64_t) * (t->n_leaves > 0 ? t->n_leaves : 1));
     if (e == cudaSuccess)

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(bp.rgb_fwd + 3 * ray + c);
             } else {
                 ShadeVisitor<K, T, false> sv{sig_arr, sh_arr, nullptr, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0, nullptr};
-                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, p.near, p.far, sv);
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, wst, o, d, p.near, p.far, sv);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) gv.ctot[c] = fmaf(sv.Tr, p.bg[c], sv.col[c]);
             }
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
                 for (int c = 0; c < 3; ++c) gv.g[c] = __ldg(bp.grad_rgb + 3 * ray + c);
             }
             if (gv.g[0] != 0.f || gv.g[1] != 0.f || gv.g[2] != 0.f)
-                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, p.near, p.far, gv);
+                walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, wst, o, d, p.near, p.far, gv);
         }
         if (MODE == kMseTarget) {
 #pragma unroll

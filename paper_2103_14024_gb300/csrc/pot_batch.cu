@@ -18,6 +18,7 @@ namespace {
 struct BatchItem {
     const int32_t *child;
     const int32_t *cells;
+    const int32_t *btab;
     const void *sigma;
     const void *sh;
     const void *codebook;
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
             RenderParams p;
             p.child = it.child;
             p.cells = it.cells;
+            p.btab = it.btab;
             p.depth = it.depth;
             p.R = it.R;
             p.lo[0] = it.lo[0];
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
             const T *sig_arr = static_cast<const T *>(it.sigma);
             const T *sh_arr = static_cast<const T *>(it.sh);
             ShadeVisitor<K, T, false> v{sig_arr, sh_arr, nullptr, it.gamma, {0.f, 0.f, 0.f}, 1.f, 0, it.codebook};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, c->near, c->far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, wst, o, d, c->near, c->far, v);
             const int64_t px = (int64_t)j * it.W + i;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) it.rgb[3 * px + ch] = fmaf(v.Tr, it.bg[ch], v.col[ch]);
@@ -139,6 +141,7 @@ cudaError_t launch_render_batch(const pot_render_item *items, int n, cudaStream_
         BatchItem &b = desc[k];
         b.child = t->child;
         b.cells = t->cells;
+        b.btab = t->btab;
         b.sigma = t->sigma;
         b.sh = t->sh;
         b.codebook = t->codebook;

@@ -382,14 +382,92 @@ __global__ void k_dist_apply(int D, const uint8_t *f, int32_t *cells)
     }
 }
 
-// Index entries in x-major voxel order (export).
-__global__ void k_cell_index_export(int D, const int32_t *cells, int32_t *out)
+// Index entries in x-major voxel order (export), from either layout.
+__global__ void k_cell_index_export(int D, const int32_t *cells, const int32_t *btab, int32_t *out)
 {
     const int64_t n = 1ll << (3 * D);
     const uint32_t m = (1u << D) - 1u;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
-        out[v] = cells[cell_index_offset(x, y, z, D)];
+        if (btab) {
+            const int32_t b = btab[brick_of(x, y, z, D)];
+            out[v] = b >= 0 ? cells[((int64_t)b << 6) | in_brick(x, y, z)] : b;
+        } else {
+            out[v] = cells[cell_index_offset(x, y, z, D)];
+        }
+    }
+}
+
+// ---- brick layout -----------------------------------------------------------
+// Per 4^3 brick (x-major over the (2^(D-2))^3 brick grid): the descent of the
+// child array along the brick's path.  A brick holding a leaf is an existing
+// node of level D - 2: its node index (> 0) is recorded and its distance seed
+// is 0; otherwise the empty node of level l around it, cell_code_node(l), and
+// the seed is the cap.
+__global__ void k_brick_classify(int D, const int32_t *child, int32_t *node_or_code, uint8_t *dist)
+{
+    const int nb = D - 2;
+    const int64_t n = brick_count(D);
+    const uint32_t m = (1u << nb) - 1u;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t bx = (uint32_t)(b >> (2 * nb)), by = (uint32_t)(b >> nb) & m, bz = (uint32_t)b & m;
+        int32_t node = 0, code = 0;
+        for (int l = 0; l < nb; ++l) {
+            const int bit = nb - 1 - l;
+            const int slot = (int)((((bx >> bit) & 1u) << 2) | (((by >> bit) & 1u) << 1) | ((bz >> bit) & 1u));
+            const int32_t c = child[(int64_t)node * 8 + slot];
+            if (c > 0) {
+                node = c;
+                continue;
+            }
+            code = cell_code_node(l + 1);  // an empty slot of a level-l node
+            break;
+        }
+        node_or_code[b] = code ? code : node;
+        dist[b] = code ? (uint8_t)kDistCap : 0;
+    }
+}
+
+__global__ void k_brick_flags(int64_t n, const int32_t *node_or_code, int *flags)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x)
+        flags[b] = node_or_code[b] > 0 ? 1 : 0;
+}
+
+// Brick codes and the entries of bricks holding a leaf.  A brick at
+// Chebyshev distance db (in bricks, capped) from the nearest brick with a leaf
+// has no leaf within 4 (db - 1) voxels of any of its voxels, so the cube of
+// that half-extent centred on any of them is empty; it replaces the empty node
+// where it is larger (the dense layout's rule).  Inside a brick with a leaf,
+// each voxel is a leaf or lies in an empty node of level D - 1 or D.
+__global__ void k_brick_fill(int D, const int32_t *child, const int32_t *node_or_code, const int *ids,
+                             const uint8_t *dist, int32_t *btab, int32_t *bricks)
+{
+    const int64_t n = brick_count(D);
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = node_or_code[b];
+        if (v > 0) {
+            const int32_t id = ids[b] - 1;
+            btab[b] = id;
+            int32_t *out = bricks + ((int64_t)id << 6);
+            for (int in = 0; in < 64; ++in) {
+                const int x = in >> 4, y = (in >> 2) & 3, z = in & 3;
+                const int s1 = ((x >> 1) << 2) | ((y >> 1) << 1) | (z >> 1);
+                const int32_t c = child[(int64_t)v * 8 + s1];
+                int32_t e;
+                if (c > 0) {
+                    const int32_t c2 = child[(int64_t)c * 8 + (((x & 1) << 2) | ((y & 1) << 1) | (z & 1))];
+                    e = c2 < 0 ? -c2 - 1 : cell_code_node(D);
+                } else {
+                    e = cell_code_node(D - 1);
+                }
+                out[in] = e;
+            }
+        } else {
+            const int level = (-v - 2) >> 1;
+            const int eb = min(4 * ((int)dist[b] - 1), kCellCubeMax);
+            btab[b] = (2 * eb + 2 > (1 << (D - level))) ? cell_code_cube(eb) : v;
+        }
     }
 }
 
@@ -400,13 +478,90 @@ cudaError_t export_cell_index(const pot_tree *t, int32_t *out, cudaStream_t s)
     const int D = t->desc.depth;
     const int64_t n = 1ll << (3 * D);
     const int64_t want = (n + 255) / 256;
-    k_cell_index_export<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(D, t->cells, out);
+    k_cell_index_export<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, s>>>(D, t->cells, t->btab, out);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t build_cell_index(pot_tree *t, cudaStream_t s)
+void free_cell_index(pot_tree *t)
 {
+    if (t->cells) cudaFree(t->cells);
+    if (t->btab) cudaFree(t->btab);
+    t->cells = nullptr;
+    t->btab = nullptr;
+    t->n_bricks = 0;
+    t->cell_kind = POT_CELLS_NONE;
+    t->index_bytes = 0;
+}
+
+namespace {
+
+cudaError_t build_brick_index(pot_tree *t, cudaStream_t s)
+{
+    const int D = t->desc.depth;
+    if (D < kBrickIndexMinDepth || D > kBrickIndexMaxDepth) return cudaErrorNotSupported;
+    const int64_t n = brick_count(D);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (n + 255) / 256, cap = (int64_t)sms * 16;
+    const unsigned g = (unsigned)(want < cap ? want : cap);
+    int32_t *node_or_code = nullptr, *btab = nullptr, *bricks = nullptr;
+    int *flags = nullptr, *ids = nullptr;
+    uint8_t *d0 = nullptr, *d1 = nullptr;
+    e = cudaMallocAsync(&node_or_code, sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&flags, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&ids, sizeof(int) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d0, (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d1, (size_t)n, s);
+    int last_id = 0;
+    if (e == cudaSuccess) {
+        k_brick_classify<<<g, 256, 0, s>>>(D, t->child, node_or_code, d0);
+        // Chebyshev distance in bricks to the nearest brick holding a leaf (capped)
+        k_dist_pass<<<g, 256, 0, s>>>(D - 2, 0, d0, d1);
+        k_dist_pass<<<g, 256, 0, s>>>(D - 2, 1, d1, d0);
+        k_dist_pass<<<g, 256, 0, s>>>(D - 2, 2, d0, d1);
+        k_brick_flags<<<g, 256, 0, s>>>(n, node_or_code, flags);
+        count_launch(5);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = scan_inclusive_impl(flags, ids, n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&last_id, ids + (n - 1), sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    const int64_t nb = last_id;
+    if (e == cudaSuccess) e = cudaMalloc(&btab, sizeof(int32_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&bricks, sizeof(int32_t) * 64 * (nb > 0 ? nb : 1));
+    if (e == cudaSuccess) {
+        k_brick_fill<<<g, 256, 0, s>>>(D, t->child, node_or_code, ids, d1, btab, bricks);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    if (node_or_code) cudaFreeAsync(node_or_code, s);
+    if (flags) cudaFreeAsync(flags, s);
+    if (ids) cudaFreeAsync(ids, s);
+    if (d0) cudaFreeAsync(d0, s);
+    if (d1) cudaFreeAsync(d1, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        if (btab) cudaFree(btab);
+        if (bricks) cudaFree(bricks);
+        return e;
+    }
+    t->btab = btab;
+    t->cells = bricks;
+    t->n_bricks = nb;
+    t->cell_kind = POT_CELLS_BRICK;
+    t->index_bytes = (int64_t)sizeof(int32_t) * (n + 64 * nb);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t build_cell_index(pot_tree *t, int kind, cudaStream_t s)
+{
+    if (kind == POT_CELLS_BRICK) return build_brick_index(t, s);
     const int D = t->desc.depth;
     if (D > kCellIndexMaxDepth) return cudaErrorNotSupported;
     const int64_t n = cell_index_entries(D);
@@ -446,6 +601,10 @@ cudaError_t build_cell_index(pot_tree *t, cudaStream_t s)
         return e;
     }
     t->cells = cells;
+    t->btab = nullptr;
+    t->n_bricks = 0;
+    t->cell_kind = POT_CELLS_DENSE;
+    t->index_bytes = (int64_t)sizeof(int32_t) * n;
     return cudaSuccess;
 }
 

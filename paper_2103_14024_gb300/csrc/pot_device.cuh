@@ -31,18 +31,31 @@ constexpr int kMaxDepth = 12;
 // Entries are stored in 4x4x4 bricks (bricks ordered x, y, z; inside a brick
 // x, y, z), so that a 128-byte line covers 2x4x4 voxels.
 // ------------------------------------------------------------------------
-constexpr int kCellIndexMaxDepth = 10;  // 4 * 8^10 bytes = 4.3 GB
-constexpr int kCellCubeMax = 63;        // largest cube half-extent e the build looks for
+constexpr int kCellIndexMaxDepth = 10;   // dense layout: 4 * 8^10 bytes = 4.3 GB
+constexpr int kBrickIndexMaxDepth = 11;  // brick layout: 4 * 8^9 bytes of brick codes at D = 11
+constexpr int kBrickIndexMinDepth = 3;
+constexpr int kDenseDefaultMaxDepth = 9;  // deeper trees get the brick layout by default
+constexpr int kCellCubeMax = 63;         // largest cube half-extent e the build looks for
 
 __host__ __device__ __forceinline__ int32_t cell_code_node(int level) { return -(2 + 2 * level); }
 __host__ __device__ __forceinline__ int32_t cell_code_cube(int e) { return -(3 + 2 * e); }
 
-__host__ __device__ __forceinline__ uint32_t cell_index_offset(uint32_t x, uint32_t y, uint32_t z, int D)
+// 4^3 bricks of the grid, ordered x, y, z; inside a brick x, y, z.
+__host__ __device__ __forceinline__ uint32_t brick_of(uint32_t x, uint32_t y, uint32_t z, int D)
 {
     const int nb = D > 2 ? D - 2 : 0;  // log2 of bricks per axis
-    const uint32_t brick = ((x >> 2) << (2 * nb)) | ((y >> 2) << nb) | (z >> 2);
-    return (brick << 6) | ((x & 3u) << 4) | ((y & 3u) << 2) | (z & 3u);
+    return ((x >> 2) << (2 * nb)) | ((y >> 2) << nb) | (z >> 2);
 }
+__host__ __device__ __forceinline__ uint32_t in_brick(uint32_t x, uint32_t y, uint32_t z)
+{
+    return ((x & 3u) << 4) | ((y & 3u) << 2) | (z & 3u);
+}
+// Entry of voxel (x, y, z) in the dense layout (D <= 10).
+__host__ __device__ __forceinline__ uint32_t cell_index_offset(uint32_t x, uint32_t y, uint32_t z, int D)
+{
+    return (brick_of(x, y, z, D) << 6) | in_brick(x, y, z);
+}
+__host__ __device__ __forceinline__ int64_t brick_count(int D) { return D > 2 ? 1ll << (3 * (D - 2)) : 1; }
 
 // Entries of the index of a depth-D tree (at least one brick).
 __host__ __device__ __forceinline__ int64_t cell_index_entries(int D)
@@ -225,14 +238,19 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y)
             Y[14] = ShC::c3e * z * (xx - yy);
             Y[15] = ShC::c3a * x * (xx - 3.f * yy);
             if (K > 16) {
-                const float z7 = 7.f * zz;
+                // z-polynomials in homogeneous form (x^2 + y^2 + z^2 = 1):
+                // 7z^2 - 3 = 4z^2 - 3 rho, 7z^2 - 1 = 6z^2 - rho,
+                // 35z^4 - 30z^2 + 3 = 8z^4 - 24 z^2 rho + 3 rho^2 (rho = x^2 + y^2),
+                // which avoids the cancellation of the large coefficients in fp32
+                const float rho = xx + yy;
+                const float a3 = 4.f * zz - 3.f * rho, a1 = 6.f * zz - rho;
                 Y[16] = ShC::c4a * x * y * (xx - yy);
                 Y[17] = ShC::c4b * y * z * (3.f * xx - yy);
-                Y[18] = ShC::c4c * x * y * (z7 - 1.f);
-                Y[19] = ShC::c4d * y * z * (z7 - 3.f);
-                Y[20] = ShC::c4e * (zz * (35.f * zz - 30.f) + 3.f);
-                Y[21] = ShC::c4d * x * z * (z7 - 3.f);
-                Y[22] = ShC::c4f * (xx - yy) * (z7 - 1.f);
+                Y[18] = ShC::c4c * x * y * a1;
+                Y[19] = ShC::c4d * y * z * a3;
+                Y[20] = ShC::c4e * (zz * (8.f * zz - 24.f * rho) + 3.f * rho * rho);
+                Y[21] = ShC::c4d * x * z * a3;
+                Y[22] = ShC::c4f * (xx - yy) * a1;
                 Y[23] = ShC::c4b * x * z * (xx - 3.f * yy);
                 Y[24] = ShC::c4g * (xx * (xx - 3.f * yy) - yy * (3.f * xx - yy));
             }
@@ -343,24 +361,33 @@ __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b)
         : "l"(p));
 }
 
-// The per-ray SH basis in shared memory: this thread's column of a block-wide
-// [K][THREADS] float array (consecutive threads hit consecutive banks).
-// (Rows of float4 read with 16-byte loads measured slower: with the 32-byte
-// record loads they push the render kernel past 64 registers.)
+// The per-ray SH basis in shared memory, one row of float4 per thread (a
+// leaf's 3K coefficients meet the basis in a few 16-byte loads instead of K
+// 4-byte ones: fewer issued instructions, which bind the walk).
 template <int K, int THREADS>
 struct SmemY {
+    // this thread's row of a [THREADS][kRow4] float4 array; an odd number of
+    // float4 per row keeps the 16-byte loads of 8 consecutive threads on
+    // distinct banks
+    static constexpr int kRow4 = ((K + 3) / 4) | 1;
     const float *base;
-    __device__ __forceinline__ float operator[](int k) const { return base[k * THREADS]; }
-    // yv[k] = Y_k for k0 <= k <= k1 (constant bounds once unrolled)
+    __device__ __forceinline__ float operator[](int k) const { return base[k]; }
+    // yv[k] = Y_k for k0 <= k <= k1 (constant bounds once unrolled), in 16-byte loads
     __device__ __forceinline__ void fetch(float *yv, int k0, int k1) const
     {
 #pragma unroll
-        for (int k = k0; k <= k1; ++k) yv[k] = base[k * THREADS];
+        for (int q = k0 / 4; q <= k1 / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4 *>(base)[q];
+            if (4 * q + 0 >= k0 && 4 * q + 0 <= k1) yv[4 * q + 0] = v.x;
+            if (4 * q + 1 >= k0 && 4 * q + 1 <= k1) yv[4 * q + 1] = v.y;
+            if (4 * q + 2 >= k0 && 4 * q + 2 <= k1) yv[4 * q + 2] = v.z;
+            if (4 * q + 3 >= k0 && 4 * q + 3 <= k1) yv[4 * q + 3] = v.w;
+        }
     }
-    __device__ __forceinline__ static void store(float *col, const float *Yt)
+    __device__ __forceinline__ static void store(float *row, const float *Yt)
     {
 #pragma unroll
-        for (int k = 0; k < K; ++k) col[k * THREADS] = Yt[k];
+        for (int k = 0; k < K; ++k) row[k] = Yt[k];
     }
 };
 

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) visibility_kern
         int64_t ray;
         if (tile_ray<true>(p, tile, lane, o, d, near, far, ray)) {
             MaxWeightVisitor<T> v{sig_arr, p.gamma, 1.f, max_w};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, near, far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, wst, o, d, near, far, v);
         }
     }
 }

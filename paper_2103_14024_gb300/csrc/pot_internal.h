@@ -23,7 +23,11 @@ struct pot_tree {
     int saturated;
     void *codebook;     // POT_CB16: [K][65536][4] fp16
     int cb_bits;        // POT_CB16: codebook entries used per basis function = 2^cb_bits
-    int32_t *cells;     // cell index (cell_index_entries(D) int32), or null
+    int32_t *cells;     // cell index: dense (cell_index_entries(D) int32) or the brick entries, or null
+    int32_t *btab;      // brick index: one code per 4^3 brick (brick_count(D) int32), else null
+    int64_t n_bricks;   // brick index: bricks stored entry by entry (those holding a leaf)
+    int cell_kind;      // POT_CELLS_NONE / _DENSE / _BRICK
+    int64_t index_bytes;
 };
 
 #ifndef POT_TILE_W
@@ -38,7 +42,8 @@ constexpr int kTileH = 32 / POT_TILE_W;
 // Everything a render launch needs; passed by value.
 struct RenderParams {
     const int32_t *child;
-    const int32_t *cells;  // cell index, or null (descend the child array)
+    const int32_t *cells;  // cell index (dense, or the stored bricks' entries), or null (descend the child array)
+    const int32_t *btab;   // brick index: code per 4^3 brick (>= 0: stored brick number), or null (dense)
     const void *sigma;
     const void *sh;
     const void *codebook;  // POT_CB16 trees
@@ -94,7 +99,8 @@ cudaError_t compact_dense(int depth, float tau, const float *d_sigma, const floa
 cudaError_t pack_leaves(pot_tree *t, const float *d_sigma, const float *d_sh, unsigned int *d_flags,
                         cudaStream_t s);
 cudaError_t export_leaves(const pot_tree *t, float *d_sigma, float *d_sh, cudaStream_t s);
-cudaError_t build_cell_index(pot_tree *t, cudaStream_t s);  // allocates t->cells and fills it
+cudaError_t build_cell_index(pot_tree *t, int kind, cudaStream_t s);  // allocates the index of that kind and fills it
+void free_cell_index(pot_tree *t);
 cudaError_t export_cell_index(const pot_tree *t, int32_t *out, cudaStream_t s);  // [R][R][R] x-major
 cudaError_t launch_query(const pot_tree *t, int64_t n, const float *xyz, int32_t *out, cudaStream_t s);
 cudaError_t launch_sh_basis(int K, int64_t n, const float *dirs, float *Y, cudaStream_t s);

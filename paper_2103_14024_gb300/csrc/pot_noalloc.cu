@@ -166,6 +166,7 @@ pot_status pot_render_noalloc(const pot_tree *t, const pot_camera *cams, int32_t
     memset(&p, 0, sizeof(p));
     p.child = t->child;
     p.cells = t->cells;
+    p.btab = t->btab;
     p.sigma = t->sigma;
     p.sh = t->sh;
     p.codebook = t->codebook;

@@ -44,14 +44,15 @@ constexpr int kBlock = 256;
 template <int K, typename T>
 struct Walker {
     float d[3];
-    // per-ray constants in shared memory (this thread's column, stride kBlock):
-    // A = lo - o as hi + lo parts, 1/d, and the locate margins -- 12 registers
-    // fewer across the walk, which keeps 4 blocks of 256 threads per SM without spills
-    float *st;
-    __device__ __forceinline__ float Ahi(int a) const { return st[a * kBlock]; }
-    __device__ __forceinline__ float Alo(int a) const { return st[(3 + a) * kBlock]; }
-    __device__ __forceinline__ float rd(int a) const { return st[(6 + a) * kBlock]; }
-    __device__ __forceinline__ float margin(int a) const { return st[(9 + a) * kBlock]; }
+    // per-ray constants in shared memory, one float4 per axis (A = lo - o as hi
+    // + lo parts, 1/d, the locate margin), 12 registers fewer across the walk;
+    // a thread's three float4 are 12 words apart from the next thread's, so the
+    // 16-byte loads of 8 consecutive threads hit distinct banks
+    float4 *st;
+    __device__ __forceinline__ float Ahi(int a) const { return st[a].x; }
+    __device__ __forceinline__ float Alo(int a) const { return st[a].y; }
+    __device__ __forceinline__ float rd(int a) const { return st[a].z; }
+    __device__ __forceinline__ float margin(int a) const { return st[a].w; }
     float len;
     // the per-ray SH basis lives in shared memory (this thread's part of the
     // block's array), not in 16 registers: that lets 4 blocks (32 warps) reside per SM
@@ -63,8 +64,6 @@ struct Walker {
     // centred on voxel q (a leaf is the cube of extent 0); cshape < 0: the
     // aligned octree node of 2^(-cshape - 1) voxels per axis around q
     int leaf, cshape, lvl_valid, step_i;
-    int kx[3];
-    df tcx[3];
 
     // a3: the cell of voxel nq: one load from the cell index when the tree
     // has one, else a descent from the deepest ancestor nq shares with voxel
@@ -74,7 +73,15 @@ struct Walker {
     {
         const int D = p.depth;
         if (p.cells) {
-            const int v = __ldg(p.cells + cell_index_offset((uint32_t)nq[0], (uint32_t)nq[1], (uint32_t)nq[2], D));
+            const uint32_t bk = brick_of((uint32_t)nq[0], (uint32_t)nq[1], (uint32_t)nq[2], D);
+            const uint32_t in = in_brick((uint32_t)nq[0], (uint32_t)nq[1], (uint32_t)nq[2]);
+            int v;
+            if (p.btab) {  // brick layout: the brick's code, or its stored entries
+                const int b = __ldg(p.btab + bk);
+                v = b >= 0 ? __ldg(p.cells + (((int64_t)b << 6) | in)) : b;
+            } else {
+                v = __ldg(p.cells + ((bk << 6) | in));
+            }
             const int c = -v - 2;  // empty: 2 l (octree node of level l) or 2 e + 1 (cube of half-extent e)
             out_leaf = v >= 0 ? v : -1;
             out_shape = v >= 0 ? 0 : (c & 1) ? (c >> 1) : -(1 + D - (c >> 1));
@@ -121,9 +128,9 @@ struct Walker {
         for (int a = 0; a < 3; ++a) {
             float ah, al;
             two_sum(p.lo[a], -o[a], ah, al);
-            st[a * kBlock] = ah;
-            st[(3 + a) * kBlock] = al;
-            st[(6 + a) * kBlock] = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
+            st[a].x = ah;
+            st[a].y = al;
+            st[a].z = d[a] != 0.f ? __frcp_rn(d[a]) : 0.f;
         }
         // a2: clip range in units of the ray parameter t (position o + t d)
         df tin = {near * invlen, 0.f};
@@ -151,7 +158,7 @@ struct Walker {
         // error bound of the fp32 voxel-coordinate estimate, in voxels
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            st[(9 + a) * kBlock] = (fabsf(tout.hi * d[a]) + fabsf(Ahi(a))) * invh * 3.8146973e-6f + 1e-6f;
+            st[a].w = (fabsf(tout.hi * d[a]) + fabsf(Ahi(a))) * invh * 3.8146973e-6f + 1e-6f;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             int v = locate_axis(tin, d[a], Ahi(a), Alo(a), h, invh, margin(a));
@@ -161,10 +168,6 @@ struct Walker {
         if (!p.cells) stk[0] = 0;  // the stack exists only for trees without a cell index
         descend(p, stk, q, q, leaf, cshape);
         if (POT_PREFETCH && leaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, leaf);
-        // exit plane (voxel index) and crossing time per axis, recomputed only
-        // when the plane changes (once per step inside runs of leaves)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) kx[a] = -0x40000000;
         t = tin;
         step_i = 0;
         return true;
@@ -185,17 +188,16 @@ struct Walker {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             qb[a] = cshape >= 0 ? q[a] - cshape : q[a] & ~(sz - 1);
-            if (d[a] != 0.f) {
-                const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
-                if (k != kx[a]) {
-                    kx[a] = k;
-                    tcx[a] = cross_time(k, h, Ahi(a), Alo(a), d[a], rd(a));
-                }
-                if (df_lt(tcx[a], texit)) {
-                    texit = tcx[a];
-                    ax = a;
-                }
-            }
+            // the exit plane's crossing, every step and without branches:
+            // recomputing it costs fewer issued instructions than branching on
+            // whether it moved (lanes of a warp cross different axes); it is
+            // finite for d = 0 (1/d is stored as 0) and then never chosen
+            const int k = d[a] > 0.f ? qb[a] + sz : qb[a];
+            const df c = cross_time(k, h, Ahi(a), Alo(a), d[a], rd(a));
+            const bool earlier = d[a] != 0.f && df_lt(c, texit);
+            texit.hi = earlier ? c.hi : texit.hi;
+            texit.lo = earlier ? c.lo : texit.lo;
+            ax = earlier ? a : ax;
         }
         const bool last = !df_lt(texit, tout);
         const df tend = last ? tout : texit;
@@ -207,34 +209,33 @@ struct Walker {
         // never move backwards.  A leaf's entry time is the crossing time of
         // its own face plane whichever box the ray crossed before it, so the
         // leaf segments do not depend on how empty space was stepped over.
-        bool stop = last;
+        // (few branches: each potentially divergent branch costs issue slots)
+        const bool capped = !last && step_i >= p.step_cap;
+        if (capped) *p.err = 1u;  // device error word: a plain store, no branch around an atomic
         int nq[3] = {q[0], q[1], q[2]};
         int nleaf = -1, nshape = 0;
-        if (!last) {
-            if (step_i >= p.step_cap) {
-                atomicOr(p.err, 1u);
-                stop = true;
-            } else {
-                bool outside = false;
+        bool outside = false;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a == ax) {
-                        nq[a] = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
-                        outside = nq[a] < 0 || nq[a] >= R;
-                    } else if (sz > 1 && d[a] != 0.f) {
-                        // within the cell and the grid (a cube may reach past the grid)
-                        int v = locate_axis(texit, d[a], Ahi(a), Alo(a), h, invh, margin(a));
-                        v = min(max(v, max(qb[a], 0)), min(qb[a] + sz, R) - 1);
-                        nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
-                    }
-                }
-                if (outside) {
-                    stop = true;
-                } else {
-                    descend(p, stk, nq, q, nleaf, nshape);
-                    if (POT_PREFETCH && nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
+        for (int a = 0; a < 3; ++a) {
+            const int stepped = d[a] > 0.f ? qb[a] + sz : qb[a] - 1;
+            nq[a] = a == ax ? stepped : nq[a];
+            outside = outside || (a == ax && (stepped < 0 || stepped >= R));
+        }
+        const bool stop = last || capped || outside;
+        if (sz > 1 && !stop) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a != ax && d[a] != 0.f) {
+                    // within the cell and the grid (a cube may reach past the grid)
+                    int v = locate_axis(texit, d[a], Ahi(a), Alo(a), h, invh, margin(a));
+                    v = min(max(v, max(qb[a], 0)), min(qb[a] + sz, R) - 1);
+                    nq[a] = d[a] > 0.f ? max(v, q[a]) : min(v, q[a]);
                 }
             }
+        }
+        if (!stop) {
+            descend(p, stk, nq, q, nleaf, nshape);
+            if (POT_PREFETCH && nleaf >= 0) prefetch_leaf<K, T>(sig_arr, sh_arr, nleaf);
         }
         if (leaf >= 0 && dt > 0.f) {
             if (vis(leaf, dt * len, Y())) return false;
@@ -258,10 +259,13 @@ struct Walker {
 // Declared once per kernel.
 #define POT_WALK_SHARED(K)                                          \
     extern __shared__ int32_t walk_stack_sh[];                      \
-    __shared__ float ysm_sh[(K) + 12][kBlock];                      \
+    __shared__ float4 walk_y_sh[kBlock * SmemY<K, kBlock>::kRow4];   \
+    __shared__ float4 walk_st_sh[kBlock * 3];                       \
     int32_t *stk = walk_stack_sh + threadIdx.x;                     \
-    float *ysm = &ysm_sh[0][threadIdx.x];                           \
-    (void)ysm;
+    float *ysm = reinterpret_cast<float *>(walk_y_sh + threadIdx.x * SmemY<K, kBlock>::kRow4); \
+    float4 *wst = walk_st_sh + 3 * threadIdx.x;                     \
+    (void)ysm;                                                      \
+    (void)wst;
 
 inline size_t walk_smem_bytes(bool need_stack)
 {
@@ -290,12 +294,12 @@ cudaError_t persistent_grid(Fn fn, size_t smem, int64_t n_tiles, int max_blocks,
 // The whole walk of one ray.
 template <int K, typename T, typename Visitor>
 __device__ __forceinline__ void walk_ray(const RenderParams &p, const T *sig_arr, const T *sh_arr,
-                                         int32_t *stk, float *ysm, const float o[3], const float d[3],
+                                         int32_t *stk, float *ysm, float4 *wst, const float o[3], const float d[3],
                                          float near, float far, Visitor &vis)
 {
     Walker<K, T> w;
     w.ysm = ysm;
-    w.st = ysm + (K) * kBlock;
+    w.st = wst;
     if (!w.begin(p, stk, sig_arr, sh_arr, o, d, near, far)) return;
     while (w.step(p, stk, sig_arr, sh_arr, vis)) {
     }
@@ -411,7 +415,7 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) render_kernel(c
         if (tile_ray<CAMS>(p, tile, lane, o, d, near, far, ray)) {
             ShadeVisitor<K, T, COUNT> v{sig_arr, sh_arr, p.leaf_touched, p.gamma, {0.f, 0.f, 0.f}, 1.f, 0,
                                         p.codebook};
-            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, o, d, near, far, v);
+            walk_ray<K, T>(p, sig_arr, sh_arr, stk, ysm, wst, o, d, near, far, v);
             store_ray<K, T, COUNT>(p, ray, v);
         }
     }
