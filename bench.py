@@ -354,14 +354,35 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
                 t_parts[name].append(ev[k].elapsed_time(ev[k + 1]))
     t_bwd = t_parts["backward"]
     t_step = [sum(v) for v in zip(*t_parts.values())]
+    # the last batch's leaf counts (a counting forward, outside the timed loop) for the
+    # backward's roofline: every distinct leaf's record read once and its gradient row
+    # (1 + 3K floats) read and written once from DRAM; the rays' origins, directions,
+    # upstream gradients and forward colours read once
+    seg = torch.zeros(B, dtype=torch.int32, device="cuda")
+    touched = torch.zeros(L, dtype=torch.uint8, device="cuda")
+    pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0, seg_count=seg, leaf_touched=touched)
+    uniq, segs = int(touched.sum().item()), int(seg.sum().item())
+    leaf_b, grad_b = int(info["leaf_bytes"]), 4 * (1 + 3 * K)
+    bwd_bytes = uniq * (leaf_b + 2 * grad_b) + B * 4 * (3 + 3 + 3 + 3)
+    bwd_l2 = segs * (leaf_b + grad_b) + B * 4 * 12
     psnr1 = held_psnr()
     pot.check()
     tree.free()
     mb, ms = sum(t_bwd) / len(t_bwd), sum(t_step) / len(t_step)
+    hbm_peak, hbm_kind = measured_peaks()
     return {"workload": f"fit a perturbed main tree to {args.train_views} training views of 800x800 (hemisphere), MSE",
             "rays_per_batch": B, "optimizer": args.train_opt, "lr_sigma": args.train_lr_sigma,
             "lr_sh": args.train_lr_sh, "steps": args.train_steps,
             "bwd_mrays_s": round(B / (mb * 1e-3) / 1e6, 2), "bwd_ms": round(mb, 4),
+            "bwd_roofline": {"bound": "hbm", "algorithmic_bytes": bwd_bytes,
+                             "achieved": round(bwd_bytes / (mb * 1e-3) / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+                             "frac": round(bwd_bytes / (mb * 1e-3) / 1e9 / hbm_peak, 4),
+                             "peak_source": f"hbm_gbs of {hbm_kind}",
+                             "unique_leaves": uniq, "leaf_segments": segs,
+                             "touched_bytes": bwd_l2,
+                             "touched_gbs": round(bwd_l2 / (mb * 1e-3) / 1e9, 1),
+                             "bytes": "distinct leaves x (record + 2 x gradient row) + rays x 48 B; touched = "
+                                      "segments x (record + gradient row) + rays x 48 B"},
             "bwd_launch": ("pot_render_mse_backward: colour walk + MSE + gradient walk" if args.train_fused
                            else "pot_render_backward with the forward colour given"),
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
@@ -455,6 +476,9 @@ def main():
                     help="extra leaf dtypes to time ('' for none); '<dtype>-descent' = that tree without its "
                          "cell index (cells located by descending the child array); '<dtype>-brick' = with the "
                          "brick layout of the cell index instead of the dense one")
+    ap.add_argument("--cells", default="default", choices=["default", "descent", "brick"],
+                    help="cell index of the main measurement's tree: its default layout, none (descend the "
+                         "child array) or the brick layout")
     ap.add_argument("--partition", default="views", choices=["views", "replicate"],
                     help="N > 1: split the views across the ranks (each ray once, strong scaling) or let "
                          "every rank render all of them (weak scaling)")
@@ -561,7 +585,8 @@ def main():
             del host
         return res
 
-    main_res = measure(args.dtype, e2e=not args.no_e2e)
+    main_key = args.dtype if args.cells == "default" else f"{args.dtype}-{args.cells}"
+    main_res = measure(main_key, e2e=not args.no_e2e)
     leaf_bytes = int(main_res["info"]["leaf_bytes"])
     alg = algorithmic_bytes(pot, torch, main_res["tree"], cams, args.dtype, leaf_bytes)
 
@@ -580,7 +605,7 @@ def main():
             l2_peak = pot.probe_l2_read(32 << 20, 200)
         except Exception:  # noqa: BLE001
             l2_peak = None
-    units = measured_units(args.dtype, sha, avg_launch_ms, len(cams), main_res["clk"].get("sm_mhz"), l2_peak, peak)
+    units = measured_units(main_key, sha, avg_launch_ms, len(cams), main_res["clk"].get("sm_mhz"), l2_peak, peak)
     traffic = units["dram"]["bytes_per_launch"] if units else None
 
     line = {
@@ -590,6 +615,7 @@ def main():
         "scaling": scaling, "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": dict(workload_config(scene, args.dtype, len(all_cams)),
                        cell_index_bytes=int(main_res["info"]["index_bytes"]),
+                       cell_index={0: "none", 2: "dense", 3: "brick"}[int(main_res["info"]["index_kind"])],
                        partition=(f"views split across {world} ranks (rank 0: views {v0}..{v1 - 1})"
                                   if args.partition == "views" and world > 1 else
                                   f"every rank renders all {len(all_cams)} views" if world > 1 else "one GPU")),
@@ -620,7 +646,7 @@ def main():
     variants = {}
     # per-GPU characteristics (other leaf types, training, serving) are measured at N = 1 only
     extras = world == 1
-    for vd in [v for v in args.variants.split(",") if v and v != args.dtype and extras]:
+    for vd in [v for v in args.variants.split(",") if v and v != main_key and extras]:
         r = measure(vd)
         w = r["wall"]
         vb = algorithmic_bytes(pot, torch, r["tree"], cams, vd.partition("-")[0], int(r["info"]["leaf_bytes"]))

@@ -324,7 +324,7 @@ __global__ void k_cell_index(int D, const int32_t *child, int32_t *cells)
                     continue;
                 }
                 // an empty slot of a level-l node is an empty level-(l+1) node
-                v = c < 0 ? -c - 1 : cell_code_node(l + 1);
+                v = c < 0 ? -c - 1 : cell_code_node(l + 1, D);
                 break;
             }
         }
@@ -376,7 +376,7 @@ __global__ void k_dist_apply(int D, const uint8_t *f, int32_t *cells)
         const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
         int32_t &c = cells[cell_index_offset(x, y, z, D)];
         if (c >= 0) continue;
-        const int level = (-c - 2) >> 1;
+        const int level = cell_code_node_level(c, D);
         const int e = (int)f[v] - 1;
         if (2 * e + 2 > (1 << (D - level))) c = cell_code_cube(e);
     }
@@ -391,9 +391,9 @@ __global__ void k_cell_index_export(int D, const int32_t *cells, const int32_t *
         const uint32_t x = (uint32_t)(v >> (2 * D)), y = (uint32_t)(v >> D) & m, z = (uint32_t)v & m;
         if (btab) {
             const int32_t b = btab[brick_of(x, y, z, D)];
-            out[v] = b >= 0 ? cells[((int64_t)b << 6) | in_brick(x, y, z)] : b;
+            out[v] = cell_code_public(b >= 0 ? cells[((int64_t)b << 6) | in_brick(x, y, z)] : b, D);
         } else {
-            out[v] = cells[cell_index_offset(x, y, z, D)];
+            out[v] = cell_code_public(cells[cell_index_offset(x, y, z, D)], D);
         }
     }
 }
@@ -420,7 +420,7 @@ __global__ void k_brick_classify(int D, const int32_t *child, int32_t *node_or_c
                 node = c;
                 continue;
             }
-            code = cell_code_node(l + 1);  // an empty slot of a level-l node
+            code = cell_code_node(l + 1, D);  // an empty slot of a level-l node
             break;
         }
         node_or_code[b] = code ? code : node;
@@ -457,14 +457,14 @@ __global__ void k_brick_fill(int D, const int32_t *child, const int32_t *node_or
                 int32_t e;
                 if (c > 0) {
                     const int32_t c2 = child[(int64_t)c * 8 + (((x & 1) << 2) | ((y & 1) << 1) | (z & 1))];
-                    e = c2 < 0 ? -c2 - 1 : cell_code_node(D);
+                    e = c2 < 0 ? -c2 - 1 : cell_code_node(D, D);
                 } else {
-                    e = cell_code_node(D - 1);
+                    e = cell_code_node(D - 1, D);
                 }
                 out[in] = e;
             }
         } else {
-            const int level = (-v - 2) >> 1;
+            const int level = cell_code_node_level(v, D);
             const int eb = min(4 * ((int)dist[b] - 1), kCellCubeMax);
             btab[b] = (2 * eb + 2 > (1 << (D - level))) ? cell_code_cube(eb) : v;
         }

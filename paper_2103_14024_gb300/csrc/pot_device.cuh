@@ -21,15 +21,16 @@ constexpr int kMaxDepth = 12;
 
 // ------------------------------------------------------------------------
 // cell index: for every voxel of the 2^D grid, the leaf that holds it (>= 0),
-// or, for an empty voxel, the empty box a ray may cross in one step:
-//   -(2 + 2 l)      the empty octree node of level l around the voxel
-//                   (2^(D-l) voxels per axis, aligned), or
-//   -(3 + 2 e)      the cube of (2e+1)^3 voxels centred on it, all empty
-//                   (e < the voxel's Chebyshev distance to the nearest leaf).
-// Locating a cell (the octree descent of Sec. 3.2 "Rendering") becomes one
-// 4-byte load, and empty space is crossed in steps of whichever box is larger.
-// Entries are stored in 4x4x4 bricks (bricks ordered x, y, z; inside a brick
-// x, y, z), so that a 128-byte line covers 2x4x4 voxels.
+// or, for an empty voxel, the empty box a ray may cross in one step: the
+// empty octree node of level l around the voxel (2^(D-l) voxels per axis,
+// aligned), or the cube of (2e+1)^3 voxels centred on it, all empty (e < the
+// voxel's Chebyshev distance to the nearest leaf).  Locating a cell (the
+// octree descent of Sec. 3.2 "Rendering") becomes one 4-byte load (dense
+// layout) or two (brick layout), and empty space is crossed in steps of
+// whichever box is larger.  Dense entries are stored in 4x4x4 bricks (bricks
+// ordered x, y, z; inside a brick x, y, z), so that a 128-byte line covers
+// 2x4x4 voxels; the brick layout keeps one code per brick and stores the 64
+// entries only of bricks that hold a leaf.
 // ------------------------------------------------------------------------
 constexpr int kCellIndexMaxDepth = 10;   // dense layout: 4 * 8^10 bytes = 4.3 GB
 constexpr int kBrickIndexMaxDepth = 11;  // brick layout: 4 * 8^9 bytes of brick codes at D = 11
@@ -37,8 +38,20 @@ constexpr int kBrickIndexMinDepth = 3;
 constexpr int kDenseDefaultMaxDepth = 9;  // deeper trees get the brick layout by default
 constexpr int kCellCubeMax = 63;         // largest cube half-extent e the build looks for
 
-__host__ __device__ __forceinline__ int32_t cell_code_node(int level) { return -(2 + 2 * level); }
-__host__ __device__ __forceinline__ int32_t cell_code_cube(int e) { return -(3 + 2 * e); }
+// Stored form of an empty entry: the walker's cell shape minus 64 (cube of
+// half-extent e: shape e; node of level l: shape -(1 + D - l)), so that the
+// walker decodes it with one addition; the public form (export) is
+// -(2 + 2 l) / -(3 + 2 e).
+constexpr int kShapeBias = 64;
+__host__ __device__ __forceinline__ int32_t cell_code_node(int level, int D) { return -(1 + D - level) - kShapeBias; }
+__host__ __device__ __forceinline__ int32_t cell_code_cube(int e) { return e - kShapeBias; }
+__host__ __device__ __forceinline__ int cell_code_node_level(int32_t v, int D) { return D + 1 + (v + kShapeBias); }
+__host__ __device__ __forceinline__ int32_t cell_code_public(int32_t v, int D)
+{
+    if (v >= 0) return v;
+    const int s = v + kShapeBias;
+    return s >= 0 ? -(3 + 2 * s) : -(2 + 2 * (D + 1 + s));
+}
 
 // 4^3 bricks of the grid, ordered x, y, z; inside a brick x, y, z.
 __host__ __device__ __forceinline__ uint32_t brick_of(uint32_t x, uint32_t y, uint32_t z, int D)
@@ -392,8 +405,9 @@ struct SmemY {
 };
 
 // x_c = sum_k sh[k][c] Y_k for the three channels of one leaf.  The record
-// is read in chunks of 64 bytes (two 32-byte or four 16-byte loads) to bound
-// live registers; each chunk fetches the basis values it multiplies.
+// is read in chunks of 96 bytes (three 32-byte or six 16-byte loads; for
+// K = 16 a chunk meets whole float4 of the basis) to bound live registers;
+// each chunk fetches the basis values it multiplies.
 template <int K, typename T, typename YT>
 __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const YT &Y, float *x, const void *)
 {
@@ -401,7 +415,7 @@ __device__ __forceinline__ void leaf_sh_dot(const T *sh, int64_t leaf, const YT 
     constexpr int N = 3 * K;
     constexpr int NV = (N + V - 1) / V;  // 16-byte units per record
     constexpr bool WIDE = POT_LDG256 && NV % 2 == 0;
-    constexpr int CH = 4;                // 16-byte units per chunk
+    constexpr int CH = 6;                // 16-byte units per chunk (96 bytes: the basis in whole float4)
     const uint4 *p = reinterpret_cast<const uint4 *>(sh + leaf * (int64_t)(NV * V));
     x[0] = x[1] = x[2] = 0.f;
     constexpr bool PACKED = POT_FFMA2 && sizeof(T) == 2;

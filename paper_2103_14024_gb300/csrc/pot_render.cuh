@@ -82,9 +82,8 @@ struct Walker {
             } else {
                 v = __ldg(p.cells + ((bk << 6) | in));
             }
-            const int c = -v - 2;  // empty: 2 l (octree node of level l) or 2 e + 1 (cube of half-extent e)
             out_leaf = v >= 0 ? v : -1;
-            out_shape = v >= 0 ? 0 : (c & 1) ? (c >> 1) : -(1 + D - (c >> 1));
+            out_shape = v >= 0 ? 0 : v + kShapeBias;  // stored as the cell shape - 64
             return;
         }
         const unsigned diff = (unsigned)((nq[0] ^ pq[0]) | (nq[1] ^ pq[1]) | (nq[2] ^ pq[2]));
