@@ -31,13 +31,43 @@ METRIC = "Mrays/s @800^2 SH-3 (200 views, depth-9 octree, gamma 1e-4)"
 UNIT = "Mrays/s"
 N_VIEWS, W, H, GAMMA = 200, 800, 800, 1e-4
 
-# Per-launch counters of the render kernel from the committed ncu captures
-# (profiles/render_kernel_main_units.md): one 16-view group of the benchmark
-# launch (the 200-view launch renders 12.5 such groups, and every counter
-# grows with the groups rendered).  Used only while the kernel sources still
+# Per-launch counters of the render kernel from ncu captures (metrics
+# gpu__time_duration, dram__bytes_read/write, lts__t_bytes, smsp__inst_executed,
+# l1tex__data_pipe_lsu_wavefronts and its fraction of peak, smsp__issue_active)
+# of one 16-view group of the benchmark launch (the 200-view launch renders
+# 12.5 such groups, and every counter grows with the groups rendered).  Used only while the kernel sources still
 # hash to ``sha``; a changed kernel reports null until it is captured again.
 NCU_VIEWS = 16
+SHA = "4da8991c6488900b"
 NCU_PROFILE = {
+    "f32": {"sha": SHA, "dram_read": 1973842432, "dram_write": 106398976,
+             "lts_bytes": 26130071200, "warp_inst": 3258636500,
+             "l1_wavefronts": 1330732707, "l1_pct": 93.15,
+             "issue_pct": 57.44, "ncu_ms": 4.5412},
+    "f16": {"sha": SHA, "dram_read": 591663872, "dram_write": 102812416,
+             "lts_bytes": 11626363488, "warp_inst": 3431872882,
+             "l1_wavefronts": 718092028, "l1_pct": 68.33,
+             "issue_pct": 82.4, "ncu_ms": 3.3432},
+    "bf16": {"sha": SHA, "dram_read": 606954240, "dram_write": 103029504,
+             "lts_bytes": 11554642368, "warp_inst": 3431863482,
+             "l1_wavefronts": 716376509, "l1_pct": 64.99,
+             "issue_pct": 78.66, "ncu_ms": 3.5039},
+    "cb16": {"sha": SHA, "dram_read": 284071424, "dram_write": 100247296,
+             "lts_bytes": 68997314880, "warp_inst": 4006563354,
+             "l1_wavefronts": 1686734406, "l1_pct": 78.09,
+             "issue_pct": 46.73, "ncu_ms": 6.8701},
+    "f32-descent": {"sha": SHA, "dram_read": 1528093952, "dram_write": 103987968,
+             "lts_bytes": 30094778912, "warp_inst": 4770991233,
+             "l1_wavefronts": 1348879191, "l1_pct": 73.61,
+             "issue_pct": 65.85, "ncu_ms": 5.8252},
+    "f32-brick": {"sha": SHA, "dram_read": 1594299392, "dram_write": 103800576,
+             "lts_bytes": 25630766816, "warp_inst": 3495248667,
+             "l1_wavefronts": 1337978636, "l1_pct": 91.58,
+             "issue_pct": 60.26, "ncu_ms": 4.6458},
+    "f16-brick": {"sha": SHA, "dram_read": 390834688, "dram_write": 101307904,
+             "lts_bytes": 11399580960, "warp_inst": 3669975306,
+             "l1_wavefronts": 747193742, "l1_pct": 65.16,
+             "issue_pct": 80.91, "ncu_ms": 3.6452},
 }
 
 
@@ -257,7 +287,7 @@ def measured_units(variant, sha, launch_ms, n_views, sm_mhz, l2_peak, hbm_peak):
     scale = n_views / NCU_VIEWS
     t = launch_ms * 1e-3
     sms = 152
-    out = {"source": f"ncu, {NCU_VIEWS}-view capture x {scale:g} (profiles/render_kernel_main_units.md)"}
+    out = {"source": f"ncu counters of a {NCU_VIEWS}-view launch of this kernel version, x {scale:g}"}
     dram = (prof["dram_read"] + prof["dram_write"]) * scale
     out["dram"] = {"bytes_per_launch": round(dram), "achieved_gbs": round(dram / t / 1e9, 1), "peak_gbs": hbm_peak,
                    "frac": round(dram / t / 1e9 / hbm_peak, 4)}
@@ -630,6 +660,8 @@ def main():
     }
     if units:
         line["roofline"]["measured_units"] = units
+    if l2_peak:
+        line["roofline"]["l2_probe_gbs"] = round(l2_peak, 1)
     line["roofline"]["touched_bytes_per_launch"] = alg["touched_bytes"]
     if rank == 0:
         line["counts"] = {"unique_leaves_summed_over_views": alg["unique_leaves"],
