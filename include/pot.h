@@ -79,7 +79,7 @@ typedef enum pot_dtype {
     POT_F32 = 0,
     POT_F16 = 1,
     POT_BF16 = 2,
-    POT_CB16 = 3 /* codebook-quantised SH (pot_tree_quantize only): fp16 sigma, uint16 codes */
+    POT_CB16 = 3 /* codebook-quantised SH (pot_tree_quantize only): float32 sigma, uint16 codes */
 } pot_dtype;
 
 typedef struct pot_tree pot_tree;
@@ -359,7 +359,8 @@ pot_status pot_tree_prune(const pot_tree *tree, const float *score, float thresh
  * App. B.2: a copy of `tree` whose SH coefficients are quantised, separately
  * for each SH basis function, into a codebook of 2^bits RGB entries (float16)
  * by median cut, each leaf keeping one uint16 code per basis function; sigma
- * is kept, stored as float16.  Median cut here: every box splits at every
+ * is kept as it is (stored as float32: the source tree's values exactly,
+ * whatever its dtype).  Median cut here: every box splits at every
  * level; the split axis is the box's longest extent (ties: lowest channel);
  * its points are ordered by (value on that axis, leaf index) and split at
  * floor(n/2); a box of fewer than two points keeps them.  An entry is the mean

@@ -364,8 +364,8 @@ def median_cut(points, bits: int):
 
 
 def quantize_scene(scene, bits: int):
-    """The scene with sigma rounded to float16 and each SH basis function's RGB
-    coefficients replaced by their median-cut codebook entries (float16),
+    """The scene with each SH basis function's RGB coefficients replaced by their
+    median-cut codebook entries (float16) and sigma kept as it is (App. B.2),
     i.e. the values a quantised tree stores; also the codebooks and codes."""
     K = scene.sh_dim
     sh = np.empty_like(scene.sh)
@@ -375,5 +375,4 @@ def quantize_scene(scene, bits: int):
         sh[:, k, :] = cb[cd].astype(np.float32)
         books.append(cb)
         codes.append(cd)
-    sig, _ = round_values(scene.sigma, "f16")
-    return scene.replace(sigma=sig, sh=sh), np.stack(books), np.stack(codes, axis=1)
+    return scene.replace(sh=sh), np.stack(books), np.stack(codes, axis=1)

@@ -557,7 +557,9 @@ pot_status pot_tree_get_info(const pot_tree *t, pot_tree_info *info)
     info->n_nodes = t->n_nodes;
     info->n_leaves = t->n_leaves;
     info->bytes = t->bytes;
-    info->leaf_bytes = (int64_t)t->elem_bytes * (1 + t->stride);  // cb16: fp16 sigma + uint16 codes
+    // cb16: float32 sigma + uint16 codes
+    info->leaf_bytes = t->desc.leaf_dtype == POT_CB16 ? 4 + 2 * (int64_t)t->stride
+                                                       : (int64_t)t->elem_bytes * (1 + t->stride);
     for (int a = 0; a < 3; ++a) info->bbox_lo[a] = t->desc.bbox_lo[a];
     info->bbox_size = t->desc.bbox_size;
     info->saturated = t->saturated;
@@ -913,7 +915,7 @@ pot_status pot_tree_quantize(const pot_tree *t, int32_t bits, pot_tree **out, po
         return cuda_fail(e, "quantize");
     }
     const int64_t n = t->n_leaves;
-    q->bytes = q->n_nodes * 32 + n * 8 + ((n * 2 + 255) / 256) * 256 + n * (int64_t)q->stride * 2 +
+    q->bytes = q->n_nodes * 32 + n * 8 + ((n * 4 + 255) / 256) * 256 + n * (int64_t)q->stride * 2 +
                (int64_t)t->K * 65536 * 8;
     e = attach_cell_index(q, s);
     if (e != cudaSuccess) {

@@ -240,7 +240,7 @@ __global__ void k_unpack(int64_t n, int K, int stride, const T *sig_in, const T 
 }
 
 // codebook leaves -> canonical float32 arrays
-__global__ void k_unpack_cb16(int64_t n, int K, int stride, const __half *sig_in, const uint16_t *codes,
+__global__ void k_unpack_cb16(int64_t n, int K, int stride, const float *sig_in, const uint16_t *codes,
                               const __half *book, float *sigma, float *sh)
 {
     const int64_t total = n * (int64_t)K;
@@ -252,7 +252,7 @@ __global__ void k_unpack_cb16(int64_t n, int K, int stride, const __half *sig_in
         const __half *e = book + ((int64_t)k * kCodebookEntries + code) * 4;
         if (sh)
             for (int c = 0; c < 3; ++c) sh[(i * K + k) * 3 + c] = __half2float(e[c]);
-        if (sigma && k == 0) sigma[i] = __half2float(sig_in[i]);
+        if (sigma && k == 0) sigma[i] = sig_in[i];
     }
 }
 
@@ -722,7 +722,7 @@ cudaError_t export_leaves(const pot_tree *t, float *d_sigma, float *d_sh, cudaSt
     if (n == 0 || (!d_sigma && !d_sh)) return cudaSuccess;
     const unsigned g = grid_for(n * 3 * t->K, 256);
     if (t->desc.leaf_dtype == POT_CB16) {
-        k_unpack_cb16<<<g, 256, 0, s>>>(n, t->K, t->stride, (const __half *)t->sigma, (const uint16_t *)t->sh,
+        k_unpack_cb16<<<g, 256, 0, s>>>(n, t->K, t->stride, (const float *)t->sigma, (const uint16_t *)t->sh,
                                         (const __half *)t->codebook, d_sigma, d_sh);
         count_launch();
         return cudaGetLastError();

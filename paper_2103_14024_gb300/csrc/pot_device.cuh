@@ -328,9 +328,9 @@ struct Store<__nv_bfloat16> {
     }
 };
 
-// Codebook-quantised leaves (App. B.2): sigma as fp16 [L]; per leaf one uint16
-// code per SH basis function, the record padded to 16 bytes; per basis
-// function a codebook of 65536 entries of 4 fp16 (R, G, B, 0).
+// Codebook-quantised leaves (App. B.2): sigma kept as it is, float32 [L]; per
+// leaf one uint16 code per SH basis function, the record padded to 16 bytes;
+// per basis function a codebook of 65536 entries of 4 fp16 (R, G, B, 0).
 struct cb16 {
 };
 constexpr int kCodebookEntries = 65536;
@@ -340,7 +340,7 @@ struct Store<cb16> {
     static constexpr int kVec = 8;  // codes per 16-byte load
     __device__ static __forceinline__ float load_sigma(const cb16 *s, int64_t i)
     {
-        return __half2float(__ldg(reinterpret_cast<const __half *>(s) + i));
+        return __ldg(reinterpret_cast<const float *>(s) + i);
     }
 };
 

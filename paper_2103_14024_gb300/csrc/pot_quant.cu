@@ -2,7 +2,8 @@
 // (App. B.2): for each SH basis function, median cut of the leaves' RGB
 // coefficients into 2^bits boxes; the codebook entry of a box is the mean of
 // its points (float64 sum in box order, rounded once to float16); each leaf
-// stores one uint16 code per basis function, sigma is kept (as float16).
+// stores one uint16 code per basis function; sigma is kept as it is (stored as
+// float32, which holds the source tree's values exactly whatever its dtype).
 //
 // Median cut, every box split at every level: the split axis is the box's
 // longest extent (ties: lowest channel); the box's points are ordered by
@@ -42,13 +43,6 @@ uint16_t half_from_double(double x)
         e += 1;
     }
     return sign | (uint16_t)((e + 15) << 10) | (uint16_t)((int)r - 1024);
-}
-
-uint16_t half_from_float_sat(float x)
-{
-    uint16_t h = half_from_double((double)x);
-    if ((h & 0x7FFF) == 0x7C00 && std::isfinite(x)) h = (h & 0x8000) | 0x7BFF;  // saturate
-    return h;
 }
 
 // points: n x 3 floats (stride 3K, offset 3k) -> codebook [C][4] halves, codes [n]
@@ -143,19 +137,13 @@ cudaError_t quantize_tree(const pot_tree *t, int bits, pot_tree *q, cudaStream_t
     }
     for (int64_t i = 0; i < L; ++i)
         for (int k = 0; k < K; ++k) codes[(size_t)i * stride + k] = per_k[k][i];
-    std::vector<uint16_t> sig16(L > 0 ? L : 1);
-    int sat = 0;
-    for (int64_t i = 0; i < L; ++i) {
-        sig16[i] = half_from_float_sat(sig[i]);
-        if ((sig16[i] & 0x7FFF) == 0x7BFF && std::fabs(sig[i]) > 65504.f) sat = 1;
-    }
-    q->saturated = sat;
+    q->saturated = t->saturated;
     q->cb_bits = bits;
-    const int64_t sig_bytes = ((L * 2 + 255) / 256) * 256;
+    const int64_t sig_bytes = ((L * 4 + 255) / 256) * 256;
     e = cudaMalloc(&q->sigma, sig_bytes > 0 ? sig_bytes : 256);
     if (e == cudaSuccess) e = cudaMalloc(&q->sh, sizeof(uint16_t) * stride * (L > 0 ? L : 1));
     if (e == cudaSuccess) e = cudaMalloc(&q->codebook, sizeof(uint16_t) * book.size());
-    if (e == cudaSuccess && L > 0) e = cudaMemcpyAsync(q->sigma, sig16.data(), 2 * L, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && L > 0) e = cudaMemcpyAsync(q->sigma, sig.data(), sizeof(float) * L, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && L > 0)
         e = cudaMemcpyAsync(q->sh, codes.data(), sizeof(uint16_t) * stride * L, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)

@@ -80,4 +80,4 @@ def test_quantize_scene_values(oracle_mod):
     assert books.shape == (sc.sh_dim, 64, 3) and codes.shape == (sc.n, sc.sh_dim)
     for k in range(sc.sh_dim):
         assert np.array_equal(q.sh[:, k, :], books[k][codes[:, k]].astype(np.float32))
-    assert np.array_equal(q.sigma, sc.sigma.astype(np.float16).astype(np.float32))
+    assert np.array_equal(q.sigma, sc.sigma)          # sigma kept as it is (App. B.2)
