@@ -52,12 +52,20 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
         if (lane == 0) tile = atomicAdd(bp.tile_counter, 1ull);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= (unsigned long long)bp.n_tiles) break;
-        // item owning the tile: last item with tile_begin <= tile
+        // item owning the tile: the last item with tile_begin <= tile, by a
+        // warp-wide search -- each round the 32 lanes test 32 evenly spaced
+        // items of [lo, hi] at once and the range shrinks to one stride (one
+        // round up to 32 items, two up to 1024), instead of a chain of
+        // dependent loads of a binary search.  items[lo].tile_begin <= tile
+        // holds throughout (item 0 begins at tile 0).
         int lo = 0, hi = bp.n_items - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (bp.items[mid].tile_begin <= (int64_t)tile) lo = mid;
-            else hi = mid - 1;
+        while (hi > lo) {
+            const int stride = (hi - lo + 32) / 32;
+            const int cand = lo + lane * stride;
+            const bool ok = cand <= hi && bp.items[cand].tile_begin <= (int64_t)tile;
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            lo += (31 - __clz(m)) * stride;
+            hi = min(hi, lo + stride - 1);
         }
         const BatchItem &it = bp.items[lo];
         const int64_t rem = (int64_t)tile - it.tile_begin;

@@ -5,13 +5,15 @@
 // until none is left (persistent grid, one wave of resident blocks).  Per ray:
 //   a1 pinhole ray (fp32 expression of the public header)
 //   a2 clip to the tree box and to [near, far]
-//   a3 locate the cell: one load from the tree's cell index (leaf, or level of
-//      the empty node, per voxel), or, for trees without one, a descent of the
-//      child array from the deepest ancestor the new voxel shares with the
-//      previous one (ancestor stack in shared memory)
-//   a4 exit time of the cell (double-float plane crossings); an empty node of
-//      any size is crossed in one step (Sec. 3.2 "Rendering")
-//   a5 leaf fetch: sigma and the SH record in 16-byte vector loads
+//   a3 locate the cell: one load from the tree's cell index (leaf, or the
+//      empty box around the voxel; two loads in the brick layout), or, for
+//      trees without one, a descent of the child array from the deepest
+//      ancestor the new voxel shares with the previous one (ancestor stack in
+//      shared memory)
+//   a4 exit time of the cell (double-float plane crossings, the earliest of
+//      three chosen with selects); an empty node of any size is crossed in one
+//      step (Sec. 3.2 "Rendering")
+//   a5 leaf fetch: sigma and the SH record in 32-byte (or 16-byte) vector loads
 //   a6 colour: sigmoid of the SH dot product, basis evaluated once per ray
 //      because it is constant along the ray (App. B.3.2)
 //   a7 composite: w = T (1 - exp(-max(sigma,0) delta)), C += w c (Eq. 1)
