@@ -441,8 +441,9 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
 def serve_measure(pot, torch, synth, args):
     """Continuous-batching server: 4 resident fp16 trees (depth 7/8/9/10, SH degree
     1/2/3/3), Poisson arrivals, resolutions from {256^2, 512^2, 800^2, 1920x1080};
-    p50/p99 latency (arrival -> completion event) and rays/s, batched vs one
-    request at a time; plus a burst (all requests at t = 0) for throughput."""
+    p50/p99 latency (arrival -> completion event) and rays/s, batched (requests of
+    up to 800x800 on a high-priority stream) vs one request at a time; plus a burst
+    (all requests at t = 0) for throughput."""
     import numpy as np
     from paper_2103_14024_gb300.serve import RenderServer, Request, summarize
     trees = []
@@ -465,7 +466,7 @@ def serve_measure(pot, torch, synth, args):
     for label, arr in (("poisson", arrival), ("burst", np.zeros_like(arrival))):
         for mode in ("batch", "alone"):
             reqs = [Request(i, float(arr[i]), int(tree_idx[i]), cams[i]) for i in range(len(cams))]
-            srv = RenderServer(trees, budget, streams=3, gamma=GAMMA)
+            srv = RenderServer(trees, budget, streams=3, gamma=GAMMA, priority_pixels=args.serve_priority_pixels)
             torch.cuda.synchronize()
             base = torch.cuda.memory_allocated()
             torch.cuda.reset_peak_memory_stats()
@@ -541,6 +542,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rate", type=float, default=300.0)
+    ap.add_argument("--serve-priority-pixels", type=int, default=800 * 800,
+                    help="requests of at most this many pixels go to a high-priority stream (0: none)")
     ap.add_argument("--views", type=int, default=N_VIEWS,
                     help="cameras per step (a smaller case for profiler captures; the benchmark uses 200)")
     args = ap.parse_args()

@@ -47,11 +47,12 @@ __global__ void __launch_bounds__(kBlock, POT_RENDER_MIN_BLOCKS) batch_kernel(co
 {
     POT_WALK_SHARED(K)
     const int lane = threadIdx.x & 31;
-    for (;;) {
-        unsigned long long tile = 0;
-        if (lane == 0) tile = atomicAdd(bp.tile_counter, 1ull);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
-        if (tile >= (unsigned long long)bp.n_tiles) break;
+    // short blocks: every warp renders one tile and the block ends, so a
+    // launch frees its SM slots tile by tile and launches of higher-priority
+    // streams (small requests) start between them
+    {
+        const unsigned long long tile = (unsigned long long)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+        if (tile >= (unsigned long long)bp.n_tiles) return;
         // item owning the tile: the last item with tile_begin <= tile, by a
         // warp-wide search -- each round the 32 lanes test 32 evenly spaced
         // items of [lo, hi] at once and the range shrinks to one stride (one
@@ -118,9 +119,9 @@ cudaError_t launch_batch_t(const BatchParams &bp, int K, bool need_stack, cudaSt
           : K == 16 ? batch_kernel<16, T> : K == 25 ? batch_kernel<25, T> : nullptr;
     if (!fn) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(need_stack);
-    unsigned grid = 0;
-    cudaError_t e = persistent_grid(fn, smem, bp.n_tiles, 0, &grid);
-    if (e != cudaSuccess) return e;
+    const int64_t blocks = (bp.n_tiles + kBlock / 32 - 1) / (kBlock / 32);
+    if (blocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(blocks > 0 ? blocks : 1);
     fn<<<grid, kBlock, smem, s>>>(bp);
     count_launch();
     return cudaGetLastError();

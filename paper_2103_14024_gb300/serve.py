@@ -6,6 +6,10 @@ the resident trees and the outputs already in flight; admitted requests are
 packed, as they come, into ``pot_render_batch`` launches (one work list per
 launch, mixed trees and resolutions) on a small ring of CUDA streams, so work
 that arrives while earlier launches run overlaps with them on the device.
+Requests of at most ``priority_pixels`` pixels go, in their own work lists,
+to a stream of higher priority: the batch kernel's blocks each render one
+tile and end, so the GPU starts their blocks between those of large
+requests already running.
 Completion is read from CUDA events; a finished request releases its budget.
 Outputs of finished requests are handed to the caller (``on_done``); when
 the caller consumes them there, device memory held by outputs stays within
@@ -72,11 +76,15 @@ class Admission:
 class RenderServer:
     def __init__(self, trees, hbm_budget_bytes: int, streams: int = 3, max_rays_per_launch: int = 8 << 20,
                  bg=(0.0, 0.0, 0.0), gamma: float = 1e-4, device="cuda", launcher=None, clock=None,
-                 allocator=None, stream_factory=None):
+                 allocator=None, stream_factory=None, priority_pixels: int = 0):
         self.trees = trees
         resident = sum(int(t.info()["bytes"]) for t in trees) if launcher is None else 0
         self.adm = Admission(hbm_budget_bytes, resident)
         self.n_streams = streams
+        # batch mode: requests of at most this many pixels are launched on a
+        # stream of higher priority (0: no such stream), so that they start
+        # between the blocks of large requests already on the GPU
+        self.priority_pixels = int(priority_pixels)
         self.max_rays = max_rays_per_launch
         self.bg, self.gamma, self.device = tuple(bg), float(gamma), device
         self.clock = clock or time.perf_counter
@@ -91,9 +99,10 @@ class RenderServer:
         return torch.empty((int(req.cam["height"]), int(req.cam["width"]), 3), dtype=torch.float32,
                            device=self.device)
 
-    def _streams_gpu(self, n):
+    def _streams_gpu(self, n, high=False):
         import torch
-        return [torch.cuda.Stream(device=self.device) for _ in range(n)]
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+        return [torch.cuda.Stream(device=self.device, priority=(hi if high else 0)) for _ in range(n)]
 
     def _launch_gpu(self, reqs, stream):
         import torch
@@ -118,6 +127,10 @@ class RenderServer:
         per_launch = None if mode == "batch" else 1
         streams = self.stream_factory(n_streams)
         free = collections.deque(range(n_streams))
+        hp = mode == "batch" and self.priority_pixels > 0
+        if hp:   # one more stream slot, of high priority, for small requests
+            streams = list(streams) + list(self.stream_factory(1, high=True))
+        hp_free = hp
         arrivals = collections.deque(requests)
         waiting = collections.deque()
         ready = collections.deque()
@@ -155,10 +168,28 @@ class RenderServer:
                             on_done(r)
                             r.rgb = None
                         self.adm.release(r.out_bytes)
-                    free.append(si)
+                    if si == n_streams:
+                        hp_free = True
+                    else:
+                        free.append(si)
                 else:
                     still.append((si, ev, reqs))
             inflight = still
+            # small requests first, on the high-priority stream
+            if hp and hp_free and any(r.rays <= self.priority_pixels for r in ready):
+                batch, rest, rays = [], collections.deque(), 0
+                for r in ready:
+                    if r.rays <= self.priority_pixels and rays + r.rays <= self.max_rays:
+                        batch.append(r)
+                        rays += r.rays
+                    else:
+                        rest.append(r)
+                ready = rest
+                t = self.clock() - t0
+                for r in batch:
+                    r.t_launch = t
+                hp_free = False
+                inflight.append((n_streams, self.launcher(batch, streams[n_streams]), batch))
             # launches: everything admitted so far (up to the ray cap) in one work list
             while ready and free:
                 batch, rays = [], 0
@@ -176,7 +207,8 @@ class RenderServer:
             # while launches are in flight, poll their events without sleeping (a
             # sleep lasts tens of microseconds, which would add to every latency);
             # sleep only when waiting for the next arrival
-            if not inflight and not (ready and free) and not (arrivals and arrivals[0].arrival <= self.clock() - t0):
+            if not inflight and not (ready and (free or hp_free)) and \
+                    not (arrivals and arrivals[0].arrival <= self.clock() - t0):
                 time.sleep(2e-5)
         return requests
 

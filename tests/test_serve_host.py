@@ -142,3 +142,41 @@ def test_on_done_hands_over_each_output_once_and_drops_it():
     assert sorted(seen) == sorted(done) and len(seen) == len(set(seen))
     assert all(r.rgb is None for r in reqs) and not live
     assert rec.max_used <= 30_000_000 and srv.adm.used == 0
+
+
+def test_small_requests_go_to_the_priority_stream():
+    """With priority_pixels, every launch on the high-priority stream slot holds
+    only requests of at most that many pixels, each request is launched once,
+    and everything completes within the budget."""
+    reqs = _requests(120, 3000.0)
+    clock = FakeClock()
+    made = []
+
+    def factory(n, high=False):
+        made.append((n, high))
+        return [("hi" if high else "lo", i) for i in range(n)]
+
+    srv = RenderServer(trees=[None] * 4, hbm_budget_bytes=60_000_000, streams=2, clock=clock,
+                       launcher=lambda *a: None, allocator=lambda r: None, stream_factory=factory,
+                       priority_pixels=512 * 512)
+    launches = []
+
+    def launcher(batch, stream):
+        launches.append((stream, [r.rid for r in batch], [r.rays for r in batch]))
+        return FakeEvent(clock, clock.t + 5e-4 + 1e-9 * sum(r.rays for r in batch))
+
+    srv.launcher = launcher
+    srv.run(reqs, mode="batch")
+    assert made == [(2, False), (1, True)]
+    hi = [l for l in launches if l[0][0] == "hi"]
+    assert hi and all(max(rays) <= 512 * 512 for _, _, rays in hi)
+    ids = [i for _, rids, _ in launches for i in rids]
+    done = [r.rid for r in reqs if not r.rejected]
+    assert sorted(ids) == sorted(done) and len(ids) == len(set(ids))
+    assert all(r.t_done >= r.t_launch >= r.t_admit >= r.arrival for r in reqs if not r.rejected)
+    # one request at a time ignores the priority stream
+    made.clear()
+    launches.clear()
+    reqs = _requests(20, 3000.0)
+    srv.run(reqs, mode="alone")
+    assert made == [(1, False)] and all(len(r) == 1 for _, r, _ in launches)
