@@ -512,7 +512,8 @@ def main():
     ap.add_argument("--variants", default="f16,bf16,cb16,f32-descent,f32-brick,f16-brick",
                     help="extra leaf dtypes to time ('' for none); '<dtype>-descent' = that tree without its "
                          "cell index (cells located by descending the child array); '<dtype>-brick' = with the "
-                         "brick layout of the cell index instead of the dense one")
+                         "brick layout of the cell index instead of the dense one; '<dtype>-batch' = the views "
+                         "rendered as a pot_render_batch work list of one item per view")
     ap.add_argument("--cells", default="default", choices=["default", "descent", "brick"],
                     help="cell index of the main measurement's tree: its default layout, none (descend the "
                          "child array) or the brick layout")
@@ -600,9 +601,14 @@ def main():
             tree.set_cell_index("brick")
         info = tree.info()
         rgb = torch.empty((len(cams), H, W, 3), dtype=torch.float32, device="cuda")
+        if mode == "batch":     # the same views as a work list of one item per view (pot_render_batch)
+            items = [(tree, cams[i], rgb[i], (0.0, 0.0, 0.0), GAMMA, None) for i in range(len(cams))]
 
-        def step():
-            pot.render(tree, ccams, rgb=rgb, gamma=GAMMA)
+            def step():
+                pot.render_batch(items)
+        else:
+            def step():
+                pot.render(tree, ccams, rgb=rgb, gamma=GAMMA)
 
         l0 = pot.launch_count()
         with ClockSampler(dev_index) as clk:

@@ -149,7 +149,10 @@ struct BackwardParams {
 enum BackwardMode { kGradAndColour = 0, kGrad = 1, kMseTarget = 2 };
 
 #ifndef POT_BACKWARD_MIN_BLOCKS
-#define POT_BACKWARD_MIN_BLOCKS 2  // 3 blocks/SM spill the gradient visitor's state (measured 10 % slower)
+// resident blocks per SM: 2 (112 registers); 3 blocks (80 registers, no
+// spills) and 4 (64, small spills) measured slower on 2^18-ray batches of the
+// main tree: 0.96 and 1.39 ms against 0.80 ms for random pixels
+#define POT_BACKWARD_MIN_BLOCKS 2
 #endif
 
 // MODE kGradAndColour: dL/dC and C given; kGrad: dL/dC given, C from a first
