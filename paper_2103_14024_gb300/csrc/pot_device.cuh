@@ -366,10 +366,24 @@ __host__ __device__ constexpr int cb_stride(int K) { return (K + 7) / 8 * 8; }
 #define POT_LDG256 1
 #endif
 
-// One 32-byte read-only load (sm_100 and later; p 32-byte aligned).
+// An 8-byte read-only load that does not allocate in L1 (codebook gathers:
+// random entries of 16 L2-resident codebooks, rarely re-read from L1).
+__device__ __forceinline__ uint2 ldg_no_l1(const uint2 *p)
+{
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
+// One 32-byte read-only load (sm_100 and later; p 32-byte aligned) that does
+// not allocate in L1: an SH record is read once per leaf segment and rarely
+// again from L1 (one sector in five hits there), while filling L1 with it
+// costs data-pipe wavefronts, which bound the kernel with float32 leaves.
+// (Measured on the main workload: f32 leaves 2178 -> 2771 Mrays/s, f16 leaves
+// 3007 -> 3042; L1 data-pipe wavefronts -30 % for f32.)
 __device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b)
 {
-    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
         : "l"(p));
 }
@@ -490,7 +504,7 @@ __device__ __forceinline__ void leaf_sh_dot_cb(const cb16 *sh, int64_t leaf, con
         const uint4 r = raw[k / 8];
         const uint32_t w = (k % 8) / 2 == 0 ? r.x : (k % 8) / 2 == 1 ? r.y : (k % 8) / 2 == 2 ? r.z : r.w;
         const uint32_t code = (k & 1) ? (w >> 16) : (w & 0xFFFFu);
-        e[k] = __ldg(book + (int64_t)k * kCodebookEntries + code);
+        e[k] = ldg_no_l1(book + (int64_t)k * kCodebookEntries + code);
     }
     x[0] = x[1] = x[2] = 0.f;
 #pragma unroll
