@@ -232,8 +232,10 @@ def test_axis_permutation_symmetry(oracle_mod):
 
 
 def test_dense_fine_step_marcher_converges(oracle_mod):
-    # Piecewise-constant field sampled at N midpoints per ray: error O(sigma * step)
-    sc = S.scene_random(16, 3, 1, p_occ=0.4, sigma_mu=0.5, sigma_s=0.5)
+    # Piecewise-constant field sampled at N midpoints per ray (SH degree 2 in
+    # its Cartesian form): the quadrature error is O(sigma * step) at each
+    # boundary a sample straddles, so it must shrink about as 1 / N.
+    sc = S.scene_random(16, 3, 2, p_occ=0.4, sigma_mu=0.5, sigma_s=0.5)
     t = oracle_mod.build_sparse(sc)
     o, d = S.random_rays(11, 25, radius=3.0, spread=0.7)
     ref = oracle_mod.render_rays(t, o, d)["rgb"]
@@ -242,12 +244,15 @@ def test_dense_fine_step_marcher_converges(oracle_mod):
     dense = -np.ones((R, R, R), dtype=np.int64)
     x, y, z = S.morton_decode(sc.morton, sc.depth)
     dense[x, y, z] = np.arange(sc.n)
+    c2 = 0.5 * math.sqrt(15.0 / math.pi)
 
     def march(i, N):
         od, dd = o[i].astype(np.float64), d[i].astype(np.float64)
         ln = float(np.linalg.norm(dd))
-        u = dd / ln
-        Y = np.array([Y00, C1 * u[1], C1 * u[2], C1 * u[0]])
+        ux, uy, uz = dd / ln
+        Y = np.array([Y00, C1 * uy, C1 * uz, C1 * ux,
+                      c2 * ux * uy, c2 * uy * uz, 0.25 * math.sqrt(5.0 / math.pi) * (3 * uz * uz - 1),
+                      c2 * ux * uz, 0.25 * math.sqrt(15.0 / math.pi) * (ux * ux - uy * uy)])
         a, b = _slab(od, dd, lo, lo + sc.bbox_size)
         if not a < b:
             return np.zeros(3)
@@ -261,11 +266,12 @@ def test_dense_fine_step_marcher_converges(oracle_mod):
         T = np.exp(-np.concatenate([[0.0], np.cumsum(x_)[:-1]]))
         return ((T * (1 - np.exp(-x_)))[:, None] * col).sum(axis=0)
 
-    for i in range(o.shape[0]):
-        e1 = np.abs(march(i, 4000) - ref[i]).max()
-        e2 = np.abs(march(i, 64000) - ref[i]).max()
-        assert e2 <= 5e-3
-        assert e2 <= e1 + 1e-9
+    e1 = np.array([np.abs(march(i, 4000) - ref[i]).max() for i in range(o.shape[0])])
+    e2 = np.array([np.abs(march(i, 64000) - ref[i]).max() for i in range(o.shape[0])])
+    assert e2.max() <= 1e-4
+    assert (e2 <= e1 + 1e-9).all()
+    assert e1.sum() > 1e-4, "the rays must cross boundaries for the rate to mean anything"
+    assert e2.sum() <= e1.sum() / 8.0  # 16 times the samples: about 16 times smaller
 
 
 def test_camera_ray_fp32_expression(oracle_mod):
