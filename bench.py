@@ -342,6 +342,7 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
     gh = torch.zeros((L, K, 3), dtype=torch.float32, device="cuda")
     B = args.train_batch
     loss_buf = torch.zeros(1, dtype=torch.float32, device="cuda")
+    records = pot.SegmentRecords.for_rays(B) if args.train_record and not args.train_fused else None
     gen = torch.Generator(device="cuda").manual_seed(1003)
     parts = ("batch", "forward", "mse", "zero", "backward", "optimizer")
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
@@ -371,15 +372,22 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
             loss, _, _ = pot.render_mse_backward(tree, o, d, y, grad_sigma=gs, grad_sh=gh, loss=loss_buf,
                                                  gamma=GAMMA, near=2.0, far=6.0)
         else:
-            rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
+            if records is not None:
+                rgb = pot.render_rays_record(tree, o, d, records, gamma=GAMMA, near=2.0, far=6.0)
+            else:
+                rgb = pot.render_rays(tree, o, d, gamma=GAMMA, near=2.0, far=6.0)
             ev[2].record()
             loss, g = pot.loss_mse(rgb, y)
             ev[3].record()
             gs.zero_()
             gh.zero_()
             ev[4].record()
-            pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0,
-                                far=6.0)
+            if records is not None:
+                pot.render_backward_recorded(tree, o, d, g, rgb, records, grad_sigma=gs, grad_sh=gh, gamma=GAMMA,
+                                             near=2.0, far=6.0)
+            else:
+                pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs, grad_sh=gh, gamma=GAMMA, near=2.0,
+                                    far=6.0)
         ev[5].record()
         opt.step(gs, gh)
         ev[6].record()
@@ -390,6 +398,7 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
                 t_parts[name].append(ev[k].elapsed_time(ev[k + 1]))
     t_bwd = t_parts["backward"]
     t_step = [sum(v) for v in zip(*t_parts.values())]
+    ab = None if args.train_fused else record_ab(pot, torch, tree, o, d, y, B, L, K)
     # the last batch's leaf counts (a counting forward, outside the timed loop) for the
     # backward's roofline: every distinct leaf's record read once and its gradient row
     # (1 + 3K floats) read and written once from DRAM; the rays' origins, directions,
@@ -420,7 +429,10 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
                              "bytes": "distinct leaves x (record + 2 x gradient row) + rays x 48 B; touched = "
                                       "segments x (record + gradient row) + rays x 48 B"},
             "bwd_launch": ("pot_render_mse_backward: colour walk + MSE + gradient walk" if args.train_fused
+                           else "pot_render_backward_recorded: one thread per segment recorded by the forward "
+                                "(pot_render_rays_record)" if records is not None
                            else "pot_render_backward with the forward colour given"),
+            "record_ab": ab,
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),
             "batch": (f"{B // 32} random 4x8-pixel tiles of the training views, one per warp"
                       if args.train_batch_mode == "tiles" else
@@ -429,13 +441,60 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
             "step_parts": ("random batch" + (" sorted by pixel" if args.train_sort else "") +
                            " + gather (torch), " +
                            ("zero grads (torch), fused forward + MSE + backward (one launch), "
-                            if args.train_fused else "forward, MSE, zero grads (torch), backward, ") +
+                            if args.train_fused else
+                            "forward recording its segments, MSE, zero grads (torch), backward over the records, "
+                            if records is not None else "forward, MSE, zero grads (torch), backward, ") +
                            "optimiser step"),
             "parts_ms": {k: round(sum(v) / len(v), 4) for k, v in t_parts.items()},
             "loss_first": round(losses[0], 6), "loss_last": round(losses[-1], 6),
             "heldout_psnr_db": {"before": psnr0, "after": psnr1,
                                 "views": f"{args.train_eval_views} held-out hemisphere views of 800x800 against "
                                          "the target tree's renders"}}
+
+
+def record_ab(pot, torch, tree, o, d, y, B, L, K, reps=10):
+    """The two training pairs on one batch (CUDA events, mean of ``reps`` after a
+    warm-up call): pot_render_rays + pot_render_backward (the backward walks
+    every ray again) against pot_render_rays_record + pot_render_backward_recorded
+    (one thread per recorded segment); and their gradients on that batch, which
+    must agree to float-atomic summation order."""
+    records = pot.SegmentRecords.for_rays(B)
+    gs = torch.zeros(L, dtype=torch.float32, device="cuda")
+    gh = torch.zeros((L, K, 3), dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    kw = dict(gamma=GAMMA, near=2.0, far=6.0)
+    rgb = pot.render_rays(tree, o, d, **kw)
+    _, g = pot.loss_mse(rgb, y)
+    out = {"forward_ms": round(timed(lambda: pot.render_rays(tree, o, d, rgb=rgb, **kw)), 4),
+           "forward_record_ms": round(timed(lambda: pot.render_rays_record(tree, o, d, records, rgb=rgb, **kw)), 4)}
+    out["backward_walk_ms"] = round(timed(lambda: pot.render_backward(tree, o, d, g, rgb_fwd=rgb, grad_sigma=gs,
+                                                                      grad_sh=gh, **kw)), 4)
+    out["backward_recorded_ms"] = round(timed(lambda: pot.render_backward_recorded(tree, o, d, g, rgb, records,
+                                                                                   grad_sigma=gs, grad_sh=gh, **kw)), 4)
+    out["records_used"] = records.used()
+    out["records_capacity"] = records.capacity
+    out["records_overflow"] = records.overflowed()
+    gs.zero_()
+    gh.zero_()
+    pot.render_backward_recorded(tree, o, d, g, rgb, records, grad_sigma=gs, grad_sh=gh, **kw)
+    ws, wh = pot.render_backward(tree, o, d, g, rgb_fwd=rgb, **kw)
+    out["recorded_vs_walk"] = {
+        "grad_sigma_max_rel": float((gs - ws).abs().max() / ws.abs().max().clamp_min(1e-30)),
+        "grad_sh_max_rel": float((gh - wh).abs().max() / wh.abs().max().clamp_min(1e-30)),
+        "bar": "max |recorded - walking| / max |walking| (float atomics: summation order only)"}
+    del records
+    return out
 
 
 def serve_measure(pot, torch, synth, args):
@@ -528,6 +587,9 @@ def main():
     ap.add_argument("--train-sort", type=int, default=1,
                     help="1: order each random ray batch by view and pixel before rendering (the sum of the "
                          "gradients does not depend on the order)")
+    ap.add_argument("--train-record", type=int, default=1,
+                    help="1: the forward records its segments and the backward differentiates the records "
+                         "(pot_render_rays_record / pot_render_backward_recorded); 0: the backward walks the rays")
     ap.add_argument("--train-fused", type=int, default=0,
                     help="1: pot_render_mse_backward (render, loss and gradients in one launch); "
                          "0: pot_render_rays + pot_loss_mse + pot_render_backward")

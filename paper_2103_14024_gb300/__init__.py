@@ -97,6 +97,8 @@ _SIGS = {
     "pot_check": [_p],
     "pot_render_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p],
     "pot_render_mse_backward": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, _p, _p, _p],
+    "pot_render_rays_record": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, C.c_int64, _p, _p],
+    "pot_render_backward_recorded": [_p, C.c_int64, _p, _p, _p, _p, _p, _p, C.c_int64, _p, _p, _p, _p],
     "pot_step": [_p, _p, _p, _p, _p, _p],
     "pot_loss_mse": [C.c_int64, _p, _p, _p, _p, _p],
     "pot_camera_rays": [_p, C.c_int32, C.c_int64, _p, _p, _p, _p],
@@ -439,6 +441,75 @@ def render_mse_backward(tree: Tree, origins, dirs, target, grad_sigma=None, grad
     return loss, grad_sigma, grad_sh
 
 
+SEGMENT_RECORD_BYTES = 32
+SEGMENT_BLOCK = 128
+
+
+class SegmentRecords:
+    """Device buffer of ``pot_render_rays_record``: ``capacity`` records of 32 bytes
+    (viewed as float32 [capacity, 8]) and the two-int64 state (slots handed out,
+    overflow flag)."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        import torch
+        self.capacity = int(capacity)
+        self.records = torch.empty((max(self.capacity, 1), 8), dtype=torch.float32, device=device)
+        self.state = torch.zeros(2, dtype=torch.int64, device=device)
+
+    @classmethod
+    def for_rays(cls, n_rays: int, segments_per_ray: int = 64, device="cuda") -> "SegmentRecords":
+        """A buffer for ``n_rays`` rays of up to ``segments_per_ray`` composited leaf
+        segments on average, plus one block of slots per resident warp."""
+        return cls(int(n_rays) * int(segments_per_ray) + 152 * 64 * SEGMENT_BLOCK, device=device)
+
+    def used(self) -> int:
+        """Slots handed out by the last recording forward (synchronises)."""
+        return int(self.state[0].item())
+
+    def overflowed(self) -> bool:
+        """Whether the last recording forward ran out of slots (synchronises)."""
+        return bool(self.state[1].item())
+
+
+def render_rays_record(tree: Tree, origins, dirs, records: SegmentRecords, rgb=None, t_final=None,
+                       bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0, far=3.0e38, want_t_final=False, stream=None):
+    """``pot_render_rays_record``: the colours of ``render_rays`` (rgb [n, 3]) and a record per
+    composited leaf segment in ``records``."""
+    import torch
+    n = int(origins.shape[0])
+    if rgb is None:
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=origins.device)
+    if want_t_final and t_final is None:
+        t_final = torch.empty(n, dtype=torch.float32, device=origins.device)
+    o = _opts(bg, gamma, near, far)
+    _check(lib().pot_render_rays_record(tree.handle, n, _ptr(origins), _ptr(dirs), C.byref(o), _ptr(rgb),
+                                        _ptr(t_final), _ptr(records.records), records.capacity,
+                                        _ptr(records.state), _stream(stream)))
+    return (rgb, t_final) if want_t_final else rgb
+
+
+def render_backward_recorded(tree: Tree, origins, dirs, grad_rgb, rgb_fwd, records: SegmentRecords,
+                             grad_sigma=None, grad_sh=None, bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0, far=3.0e38,
+                             stream=None):
+    """``pot_render_backward_recorded``: the gradients of ``render_backward`` from the records of the
+    ``render_rays_record`` call that produced ``rgb_fwd``; accumulates into (and returns) grad_sigma [L],
+    grad_sh [L, K, 3]."""
+    import torch
+    inf = tree.info()
+    L, K = inf["n_leaves"], inf["sh_dim"]
+    dev = origins.device
+    if grad_sigma is None:
+        grad_sigma = torch.zeros(L, dtype=torch.float32, device=dev)
+    if grad_sh is None:
+        grad_sh = torch.zeros((L, K, 3), dtype=torch.float32, device=dev)
+    o = _opts(bg, gamma, near, far)
+    _check(lib().pot_render_backward_recorded(tree.handle, int(origins.shape[0]), _ptr(origins), _ptr(dirs),
+                                              _ptr(grad_rgb), _ptr(rgb_fwd), C.byref(o), _ptr(records.records),
+                                              records.capacity, _ptr(records.state), _ptr(grad_sigma),
+                                              _ptr(grad_sh), _stream(stream)))
+    return grad_sigma, grad_sh
+
+
 def step_state_floats(tree: Tree, kind: str) -> int:
     return int(lib().pot_step_state_floats(tree.handle, OPTIMIZERS[kind]))
 
@@ -486,10 +557,14 @@ def _autograd_fn():
         tree's; the tree itself is updated by ``step`` or ``Tree.set_values``)."""
 
         @staticmethod
-        def forward(ctx, sigma_param, sh_param, tree, origins, dirs, bg, gamma, near, far):
-            rgb = render_rays(tree, origins, dirs, bg=bg, gamma=gamma, near=near, far=far)
+        def forward(ctx, sigma_param, sh_param, tree, origins, dirs, bg, gamma, near, far, records):
+            if records is None:
+                rgb = render_rays(tree, origins, dirs, bg=bg, gamma=gamma, near=near, far=far)
+            else:
+                rgb = render_rays_record(tree, origins, dirs, records, bg=bg, gamma=gamma, near=near, far=far)
             ctx.save_for_backward(origins, dirs, rgb)
             ctx.tree = tree
+            ctx.records = records
             ctx.cfg = (bg, gamma, near, far)
             ctx.shapes = (sigma_param.shape, sh_param.shape)
             return rgb
@@ -498,9 +573,14 @@ def _autograd_fn():
         def backward(ctx, grad_rgb):
             o, d, rgb = ctx.saved_tensors
             bg, gamma, near, far = ctx.cfg
-            gs, gh = render_backward(ctx.tree, o, d, grad_rgb.contiguous(), rgb_fwd=rgb, bg=bg, gamma=gamma,
-                                     near=near, far=far)
-            return gs.reshape(ctx.shapes[0]), gh.reshape(ctx.shapes[1]), None, None, None, None, None, None, None
+            if ctx.records is None:
+                gs, gh = render_backward(ctx.tree, o, d, grad_rgb.contiguous(), rgb_fwd=rgb, bg=bg, gamma=gamma,
+                                         near=near, far=far)
+            else:
+                gs, gh = render_backward_recorded(ctx.tree, o, d, grad_rgb.contiguous(), rgb, ctx.records, bg=bg,
+                                                  gamma=gamma, near=near, far=far)
+            return (gs.reshape(ctx.shapes[0]), gh.reshape(ctx.shapes[1]), None, None, None, None, None, None, None,
+                    None)
 
     return RenderRaysFn
 
@@ -509,13 +589,14 @@ _RenderRaysFn = None
 
 
 def render_rays_diff(tree: Tree, sigma_param, sh_param, origins, dirs, bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0,
-                     far=3.0e38):
-    """Differentiable ``render_rays`` (torch.autograd.Function around pot_render_rays / pot_render_backward)."""
+                     far=3.0e38, records: "SegmentRecords | None" = None):
+    """Differentiable ``render_rays`` (torch.autograd.Function around pot_render_rays / pot_render_backward;
+    with ``records``, around pot_render_rays_record / pot_render_backward_recorded)."""
     global _RenderRaysFn
     if _RenderRaysFn is None:
         _RenderRaysFn = _autograd_fn()
     return _RenderRaysFn.apply(sigma_param, sh_param, tree, origins, dirs, tuple(bg), float(gamma), float(near),
-                               float(far))
+                               float(far), records)
 
 
 class LeafOptimizer:

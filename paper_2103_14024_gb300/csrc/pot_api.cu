@@ -3,6 +3,7 @@
 // the kernels of pot_build.cu, pot_query.cu and pot_render_*.cu.
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,7 @@
 
 #include "pot_device.cuh"
 #include "pot_internal.h"
+#include "pot_segments_internal.h"
 
 namespace pot {
 
@@ -1029,6 +1031,128 @@ pot_status pot_render_mse_backward(const pot_tree *t, int64_t n, const float *or
     p.tile_counter = static_cast<unsigned long long *>(scratch.p);
     POT_CUDA(launch_mse_backward(p, target, rgb, loss, grad_sigma, grad_sh, t->desc.leaf_dtype, t->K, s),
              "mse backward");
+    return POT_OK;
+}
+
+namespace {
+
+// Checks shared by the two recorded-segment entry points.
+pot_status check_segment_buffer(const void *records, int64_t capacity, const int64_t *seg_state)
+{
+    if (capacity < 0 || capacity > INT32_MAX) return fail(POT_ERR_INVALID_ARG, "capacity must be in [0, 2^31)");
+    if (!seg_state || !is_device_ptr(seg_state)) return fail(POT_ERR_INVALID_ARG, "seg_state must be device memory");
+    if (capacity > 0 && (!records || !is_device_ptr(records)))
+        return fail(POT_ERR_INVALID_ARG, "records must be device memory");
+    if (((uintptr_t)records & 15u) != 0 || ((uintptr_t)seg_state & 7u) != 0)
+        return fail(POT_ERR_INVALID_ARG, "records must be 16-byte and seg_state 8-byte aligned");
+    return POT_OK;
+}
+
+}  // namespace
+
+pot_status pot_render_rays_record(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
+                                  const pot_render_opts *opts, float *rgb, float *t_final, void *records,
+                                  int64_t capacity, int64_t *seg_state, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(POT_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    pot_status st = check_segment_buffer(records, capacity, seg_state);
+    if (st != POT_OK) return st;
+    if (n > 0 && (!origins || !dirs || !rgb)) return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (n > 0 && (!is_device_ptr(origins) || !is_device_ptr(dirs) || !is_device_ptr(rgb) ||
+                  (t_final && !is_device_ptr(t_final))))
+        return fail(POT_ERR_INVALID_ARG, "pot_render_rays_record takes device arrays only");
+    st = check_opts(opts);
+    if (st != POT_OK) return st;
+    if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used when recording");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
+    if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    POT_CUDA(cudaMemsetAsync(seg_state, 0, 2 * sizeof(int64_t), s), "clear seg_state");
+    if (n == 0) return POT_OK;
+    Tmp scratch;
+    POT_CUDA(scratch.alloc(sizeof(unsigned long long), s), "alloc scratch");
+    POT_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), s), "memset");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.ray_o = origins;
+    p.ray_d = dirs;
+    p.n_rays = n;
+    p.near = near;
+    p.far = far;
+    p.n_tiles = (n + 31) / 32;
+    p.rgb = rgb;
+    p.t_final = t_final;
+    p.tile_counter = static_cast<unsigned long long *>(scratch.p);
+    const SegmentBuffer sb{static_cast<float4 *>(records), capacity, reinterpret_cast<unsigned long long *>(seg_state)};
+    POT_CUDA(launch_render_record(p, sb, t->desc.leaf_dtype, t->K, s), "render_rays_record");
+    return POT_OK;
+}
+
+pot_status pot_render_backward_recorded(const pot_tree *t, int64_t n, const float *origins, const float *dirs,
+                                        const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
+                                        const void *records, int64_t capacity, const int64_t *seg_state,
+                                        float *grad_sigma, float *grad_sh, pot_stream stream)
+{
+    if (!t) return fail(POT_ERR_INVALID_ARG, "tree is NULL");
+    if (n < 0 || n > INT32_MAX) return fail(POT_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    pot_status st = check_segment_buffer(records, capacity, seg_state);
+    if (st != POT_OK) return st;
+    if (n == 0 || t->n_leaves == 0) return POT_OK;
+    if (!origins || !dirs || !grad_rgb || !rgb_fwd || !grad_sigma || !grad_sh)
+        return fail(POT_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(origins) || !is_device_ptr(dirs) || !is_device_ptr(grad_rgb) || !is_device_ptr(rgb_fwd) ||
+        !is_device_ptr(grad_sigma) || !is_device_ptr(grad_sh))
+        return fail(POT_ERR_INVALID_ARG, "pot_render_backward_recorded takes device arrays only");
+    st = check_opts(opts);
+    if (st != POT_OK) return st;
+    if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
+    if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
+    if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
+    DeviceGuard g(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    Tmp scratch;  // tile counter of the walking fallback
+    POT_CUDA(scratch.alloc(sizeof(unsigned long long), s), "alloc scratch");
+    POT_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long), s), "memset");
+    RenderParams p;
+    fill_tree_params(p, t, opts);
+    if (!p.err) return fail(POT_ERR_CUDA, "device error word unavailable");
+    p.ray_o = origins;
+    p.ray_d = dirs;
+    p.n_rays = n;
+    p.near = near;
+    p.far = far;
+    p.n_tiles = (n + 31) / 32;
+    p.tile_counter = static_cast<unsigned long long *>(scratch.p);
+    const SegmentBuffer sb{static_cast<float4 *>(const_cast<void *>(records)), capacity,
+                           reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(seg_state))};
+    // scratch of the bin order: bins of 2^bb leaves (count, start, cursor)
+    // and the records' numbers in bin order
+    // POT_SEGBWD_ORDER (read once): 1 (default) visits the records in bin
+    // order, 0 in slot order (no scratch; faster when a batch's rays are
+    // already neighbours, e.g. whole pixel tiles)
+    static const bool direct = [] {
+        const char *e = std::getenv("POT_SEGBWD_ORDER");
+        return e && std::atoi(e) == 0;
+    }();
+    const int bb = segment_bin_log2(t->K);
+    if (bb < 0) return fail(POT_ERR_UNSUPPORTED, "SH degree not supported");
+    const int64_t nb = (t->n_leaves + (int64_t(1) << bb) - 1) >> bb;
+    Tmp bin_mem;
+    SegmentBins bins{};
+    if (!direct) {
+        POT_CUDA(bin_mem.alloc(sizeof(unsigned) * (size_t)(3 * nb + 1 + capacity), s), "alloc bins");
+        unsigned *base = static_cast<unsigned *>(bin_mem.p);
+        bins = SegmentBins{base, base + nb, base + 2 * nb + 1, base + 3 * nb + 1, nb};
+        POT_CUDA(cudaMemsetAsync(bins.count, 0, sizeof(unsigned) * (size_t)nb, s), "clear bins");
+    }
+    POT_CUDA(launch_backward_recorded(p, t->n_leaves, sb, direct ? nullptr : &bins, grad_rgb, rgb_fwd, grad_sigma,
+                                      grad_sh, t->desc.leaf_dtype, t->K, s),
+             "backward_recorded");
     return POT_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "pot_render.cuh"
+#include "pot_segments_internal.h"
 
 #ifndef POT_BWD_AGG
 // warp-aggregated gradient scatter (lanes sharing a leaf reduce by shuffles
@@ -45,6 +46,36 @@ __device__ __forceinline__ void red_add4(float *a, float x, float y, float z, fl
                  : "memory");
 }
 
+// The terms of one leaf segment (App. B.3.2), given T_i (Tr) and the colour
+// composited in front of it (prefix): the colour derivative gx_c =
+// dL/dC_c w c_c (1 - c_c) (times Y_k for coefficient k) and the density
+// derivative gsd (0 for sigma <= 0); Tr and prefix move past the segment.
+// Returns whether sigma > 0.  The same operations as the forward's shading.
+template <int K, typename T, typename YT>
+__device__ __forceinline__ bool segment_terms(const T *sig_arr, const T *sh_arr, int leaf, float delta, const YT &Y,
+                                              const float g[3], const float ctot[3], float prefix[3], float &Tr,
+                                              float gx[3], float &gsd)
+{
+    const float sraw = Store<T>::load_sigma(sig_arr, leaf);
+    const float sig = fmaxf(sraw, 0.f);
+    float x[3];
+    leaf_sh_dot<K, T>(sh_arr, leaf, Y, x, nullptr);
+    const float e = __expf(-sig * delta);  // same operations as the forward
+    const float w = Tr * (1.f - e);
+    const float Tn = Tr * e;
+    float gs = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float col = sigmoidf_(x[c]);
+        prefix[c] = fmaf(w, col, prefix[c]);
+        gx[c] = g[c] * w * col * (1.f - col);
+        gs = fmaf(g[c], fmaf(col, Tn, -(ctot[c] - prefix[c])), gs);
+    }
+    gsd = sraw > 0.f ? gs * delta : 0.f;  // zero for sigma <= 0 (same leaf: same sign)
+    Tr = Tn;
+    return sraw > 0.f;
+}
+
 template <int K, typename T>
 struct GradVisitor {
     const T *sig_arr;
@@ -59,23 +90,9 @@ struct GradVisitor {
     template <typename YT>
     __device__ __forceinline__ bool operator()(int leaf, float delta, const YT &Y)
     {
-        const float sraw = Store<T>::load_sigma(sig_arr, leaf);
-        const float sig = fmaxf(sraw, 0.f);
-        float x[3];
-        leaf_sh_dot<K, T>(sh_arr, leaf, Y, x, nullptr);
-        const float e = __expf(-sig * delta);  // same operations as the forward
-        const float w = Tr * (1.f - e);
-        const float Tn = Tr * e;
-        float gx[3], gs = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float col = sigmoidf_(x[c]);
-            prefix[c] = fmaf(w, col, prefix[c]);
-            gx[c] = g[c] * w * col * (1.f - col);
-            gs = fmaf(g[c], fmaf(col, Tn, -(ctot[c] - prefix[c])), gs);
-        }
+        float gx[3], gsd;
+        const bool pos = segment_terms<K, T>(sig_arr, sh_arr, leaf, delta, Y, g, ctot, prefix, Tr, gx, gsd);
         float *row = grad_sh + (int64_t)leaf * (3 * K);
-        float gsd = sraw > 0.f ? gs * delta : 0.f;  // zero for sigma <= 0 (same leaf: same sign)
 #if POT_BWD_AGG
         // lanes compositing the same leaf: sum over the group with a shuffle
         // tree over its members (ranked by lane); the lowest lane scatters
@@ -110,9 +127,8 @@ struct GradVisitor {
 #pragma unroll
                         for (int j = 0; j < 3 * K; ++j) red_add(row + j, v[j]);
                     }
-                    if (sraw > 0.f) red_add(grad_sigma + leaf, gsd);
+                    if (pos) red_add(grad_sigma + leaf, gsd);
                 }
-                Tr = Tn;
                 return Tr < gamma;
             }
         }
@@ -126,8 +142,7 @@ struct GradVisitor {
 #pragma unroll
             for (int j = 0; j < 3 * K; ++j) red_add(row + j, gx[j % 3] * Y[j / 3]);
         }
-        if (sraw > 0.f) red_add(grad_sigma + leaf, gsd);
-        Tr = Tn;
+        if (pos) red_add(grad_sigma + leaf, gsd);
         return Tr < gamma;
     }
 };
@@ -143,6 +158,9 @@ struct BackwardParams {
     float *loss;
     float *rgb_out;        // optional copy of C
     float mse_scale;
+    // non-null: the kernel runs only if *run_if != 0 (the walking backward as
+    // the fallback of the per-record backward, whose records overflowed)
+    const unsigned long long *run_if;
 };
 
 // What the backward kernel is given per ray.
@@ -163,6 +181,7 @@ __global__ void __launch_bounds__(kBlock, POT_BACKWARD_MIN_BLOCKS) backward_kern
 {
     POT_WALK_SHARED(K)
     const RenderParams &p = bp.r;
+    if (bp.run_if && *bp.run_if == 0ull) return;
     const int lane = threadIdx.x & 31;
     const T *sig_arr = static_cast<const T *>(p.sigma);
     const T *sh_arr = static_cast<const T *>(p.sh);
@@ -245,6 +264,250 @@ cudaError_t launch_backward_t(const BackwardParams &bp, int K, int mode, cudaStr
     fn<<<grid, kBlock, smem, s>>>(bp);
     count_launch();
     return cudaGetLastError();
+}
+
+// ---- gradients from recorded segments ---------------------------------------
+// One thread per record of pot_render_rays_record: the record gives the leaf,
+// delta_i, T_i and P_i, the ray gives dL/dC, C and the SH basis at its
+// direction; GradVisitor then does exactly the per-segment work of the walking
+// backward (same operations, so the same per-segment terms bit for bit).
+
+// The per-ray SH basis in registers (the interface of SmemY).
+template <int K>
+struct RegY {
+    float v[K];
+    __device__ __forceinline__ float operator[](int k) const { return v[k]; }
+    __device__ __forceinline__ void fetch(float *yv, int k0, int k1) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (k >= k0 && k <= k1) yv[k] = v[k];
+    }
+};
+
+struct SegBackwardParams {
+    SegmentBuffer sb;
+    int64_t n_rays;    // records naming a ray or leaf outside these ranges are skipped
+    int64_t n_leaves;
+    // non-null: visit the records in the order perm[0 .. *n_perm) (by bin of
+    // leaves, so that the reductions of neighbouring threads meet the same
+    // gradient rows in L2); null: in slot order
+    const unsigned *perm;
+    const unsigned *n_perm;
+    const void *sigma;
+    const void *sh;
+    const float *ray_d;
+    const float *grad_rgb;
+    const float *rgb_fwd;
+    float *grad_sigma;
+    float *grad_sh;
+};
+
+#ifndef POT_SEGBWD_MIN_BLOCKS
+// resident blocks per SM: 3 (at most 80 registers, no spills; 4 blocks spill 12 bytes at 64)
+#define POT_SEGBWD_MIN_BLOCKS 3
+#endif
+
+template <int K, typename T>
+__global__ void __launch_bounds__(kBlock, POT_SEGBWD_MIN_BLOCKS) segment_backward_kernel(const SegBackwardParams q)
+{
+    if (q.sb.state[1] != 0ull) return;  // the records overflowed: the walking backward runs instead
+    const unsigned long long handed = q.sb.state[0];
+    const int64_t used = q.perm ? (int64_t)*q.n_perm
+                       : handed < (unsigned long long)q.sb.capacity ? (int64_t)handed : q.sb.capacity;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < used;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q.perm ? (int64_t)q.perm[k] : k;
+        const float4 a = __ldg(q.sb.rec + 2 * i);
+        const int ray = __float_as_int(a.x);
+        const int leaf = __float_as_int(a.y);
+        if (ray < 0 || ray >= q.n_rays) continue;  // an unused slot (ray -1)
+        if (leaf < 0 || leaf >= q.n_leaves) continue;
+        GradVisitor<K, T> gv;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gv.g[c] = __ldg(q.grad_rgb + 3 * (int64_t)ray + c);
+        if (gv.g[0] == 0.f && gv.g[1] == 0.f && gv.g[2] == 0.f) continue;
+        const float4 b = __ldg(q.sb.rec + 2 * i + 1);
+        gv.sig_arr = static_cast<const T *>(q.sigma);
+        gv.sh_arr = static_cast<const T *>(q.sh);
+        gv.gamma = 0.f;
+        gv.grad_sigma = q.grad_sigma;
+        gv.grad_sh = q.grad_sh;
+        gv.Tr = a.w;
+        gv.prefix[0] = b.x;
+        gv.prefix[1] = b.y;
+        gv.prefix[2] = b.z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(q.rgb_fwd + 3 * (int64_t)ray + c);
+        float d[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) d[r] = __ldg(q.ray_d + 3 * (int64_t)ray + r);
+        // the basis exactly as the walk computes it (Walker::begin)
+        const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+        const float invlen = __frcp_rn(len);
+        RegY<K> Y;
+        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y.v);
+        gv(leaf, a.z, Y);
+    }
+}
+
+template <typename T>
+cudaError_t launch_segment_backward_t(const SegBackwardParams &q, int K, cudaStream_t s)
+{
+    using Fn = void (*)(const SegBackwardParams);
+    Fn fn = K == 1 ? segment_backward_kernel<1, T> : K == 4 ? segment_backward_kernel<4, T>
+          : K == 9 ? segment_backward_kernel<9, T> : K == 16 ? segment_backward_kernel<16, T>
+          : K == 25 ? segment_backward_kernel<25, T> : nullptr;
+    if (!fn) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0);
+    if (e != cudaSuccess) return e;
+    // one wave of resident blocks, no more than the slots could need
+    int64_t blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (q.sb.capacity + kBlock - 1) / kBlock;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    fn<<<(unsigned)blocks, kBlock, 0, s>>>(q);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---- recorded segments in bin order -----------------------------------------
+// The float reductions of the per-record kernel land on gradient rows spread
+// over all L leaves (L (1 + 3K) floats, far larger than L2).  Visiting the
+// records ordered by bin of 2^BB consecutive leaves (count, scan, scatter of
+// record numbers) makes neighbouring threads reduce into the same ~50 KB of
+// rows, which stay in L2.  (Summing each bin in shared memory and adding the
+// rows once, with no global atomics, measured slower: its blocks wait on
+// dependent loads between barriers.)
+
+// log2 of the leaves per bin: the largest 2^BB whose gradient rows,
+// (1 + 3K) floats each, fit in 64 KB.
+__host__ __device__ constexpr int bin_log2(int K)
+{
+    int b = 12;
+    while (b > 4 && (int64_t(1) << b) * (1 + 3 * K) * 4 > 65536) --b;
+    return b;
+}
+
+struct SegBinParams {
+    SegBackwardParams s;
+    const unsigned *start;  // [n_bins + 1] first sorted slot of each bin
+    unsigned *count;        // [n_bins] records per bin
+    unsigned *cursor;       // [n_bins] scatter cursors
+    unsigned *perm;         // [capacity] record numbers in bin order
+    int64_t n_bins;
+};
+
+// A record's bin, or -1 for an unused slot or one naming an out-of-range ray
+// or leaf.
+template <int BB>
+__device__ __forceinline__ int record_bin(const SegBackwardParams &q, int64_t i, int64_t used)
+{
+    if (i >= used) return -1;
+    const float4 a = __ldg(q.sb.rec + 2 * i);
+    const int ray = __float_as_int(a.x), leaf = __float_as_int(a.y);
+    if (ray < 0 || ray >= q.n_rays || leaf < 0 || leaf >= q.n_leaves) return -1;
+    return leaf >> BB;
+}
+
+__device__ __forceinline__ int64_t records_used(const SegmentBuffer &sb)
+{
+    const unsigned long long handed = sb.state[0];
+    return handed < (unsigned long long)sb.capacity ? (int64_t)handed : sb.capacity;
+}
+
+// Pass 1 (SCATTER = false): records per bin.  Pass 2 (SCATTER = true): each
+// record's number to its bin's part of perm.  Whole warps step together so
+// that lanes with the same bin (neighbouring rays of one step) share one
+// atomic, found with a match.
+template <int BB, bool SCATTER>
+__global__ void __launch_bounds__(kBlock) bin_pass_kernel(const SegBinParams q)
+{
+    if (q.s.sb.state[1] != 0ull) return;
+    const int64_t used = records_used(q.s.sb);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < used; i0 += stride) {
+        const int64_t i = i0 + lane;
+        const int b = record_bin<BB>(q.s, i, used);
+        const unsigned m = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(m) - 1;
+        if (!SCATTER) {
+            if (b >= 0 && lane == leader) atomicAdd(q.count + b, (unsigned)__popc(m));
+        } else {
+            unsigned base = 0;
+            if (b >= 0 && lane == leader) base = atomicAdd(q.cursor + b, (unsigned)__popc(m));
+            base = __shfl_sync(m, base, leader);
+            if (b >= 0) q.perm[q.start[b] + base + __popc(m & ((1u << lane) - 1u))] = (unsigned)i;
+        }
+    }
+}
+
+// Exclusive scan of the bin counts into start[0..n_bins] (one block) and
+// cleared cursors.
+__global__ void __launch_bounds__(1024) bin_scan_kernel(const SegBinParams q)
+{
+    __shared__ unsigned part[1024];
+    const int64_t nb = q.n_bins;
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t lo = threadIdx.x * per, hi = min(lo + per, nb);
+    unsigned sum = 0;
+    for (int64_t b = lo; b < hi; ++b) sum += q.count[b];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    unsigned *start = const_cast<unsigned *>(q.start);
+    for (int64_t b = lo; b < hi; ++b) {
+        start[b] = run;
+        run += q.count[b];
+        q.cursor[b] = 0u;
+    }
+    if (threadIdx.x == 1023) start[nb] = part[1023];
+}
+
+template <int K, typename T>
+cudaError_t launch_binned_k(const SegBinParams &q, cudaStream_t s)
+{
+    constexpr int BB = bin_log2(K);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // count and scatter passes: a few waves of blocks over the slots (grid-stride)
+    int64_t blocks = (q.s.sb.capacity + kBlock - 1) / kBlock;
+    if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+    if (blocks < 1) blocks = 1;
+    bin_pass_kernel<BB, false><<<(unsigned)blocks, kBlock, 0, s>>>(q);
+    bin_scan_kernel<<<1, 1024, 0, s>>>(q);
+    bin_pass_kernel<BB, true><<<(unsigned)blocks, kBlock, 0, s>>>(q);
+    count_launch(3);
+    // the per-record kernel over the records in bin order
+    SegBackwardParams sq = q.s;
+    sq.perm = q.perm;
+    sq.n_perm = q.start + q.n_bins;
+    return launch_segment_backward_t<T>(sq, K, s);
+}
+
+template <typename T>
+cudaError_t launch_binned_t(const SegBinParams &q, int K, cudaStream_t s)
+{
+    switch (K) {
+    case 1: return launch_binned_k<1, T>(q, s);
+    case 4: return launch_binned_k<4, T>(q, s);
+    case 9: return launch_binned_k<9, T>(q, s);
+    case 16: return launch_binned_k<16, T>(q, s);
+    case 25: return launch_binned_k<25, T>(q, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ---- optimiser step on the leaves ------------------------------------------
@@ -448,6 +711,44 @@ cudaError_t launch_mse_backward(const RenderParams &r, const float *target, floa
     case POT_F32: return launch_backward_t<float>(bp, K, kMseTarget, s);
     case POT_F16: return launch_backward_t<__half>(bp, K, kMseTarget, s);
     default: return launch_backward_t<__nv_bfloat16>(bp, K, kMseTarget, s);
+    }
+}
+
+int segment_bin_log2(int K)
+{
+    return (K == 1 || K == 4 || K == 9 || K == 16 || K == 25) ? bin_log2(K) : -1;
+}
+
+cudaError_t launch_backward_recorded(const RenderParams &r, int64_t n_leaves, const SegmentBuffer &sb,
+                                     const SegmentBins *bins, const float *grad_rgb, const float *rgb_fwd,
+                                     float *grad_sigma, float *grad_sh, int dtype, int K, cudaStream_t s)
+{
+    SegBackwardParams q{sb,      r.n_rays,   n_leaves, nullptr,    nullptr,   r.sigma,
+                        r.sh,    r.ray_d,    grad_rgb, rgb_fwd,    grad_sigma, grad_sh};
+    cudaError_t e;
+    if (bins) {
+        const SegBinParams bq{q, bins->start, bins->count, bins->cursor, bins->perm, bins->n_bins};
+        switch (dtype) {
+        case POT_F32: e = launch_binned_t<float>(bq, K, s); break;
+        case POT_F16: e = launch_binned_t<__half>(bq, K, s); break;
+        case POT_BF16: e = launch_binned_t<__nv_bfloat16>(bq, K, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (dtype) {
+        case POT_F32: e = launch_segment_backward_t<float>(q, K, s); break;
+        case POT_F16: e = launch_segment_backward_t<__half>(q, K, s); break;
+        case POT_BF16: e = launch_segment_backward_t<__nv_bfloat16>(q, K, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    // the fallback: every ray walked again, only if the records overflowed
+    BackwardParams bp{r, grad_rgb, rgb_fwd, grad_sigma, grad_sh, nullptr, nullptr, nullptr, 0.f, sb.state + 1};
+    switch (dtype) {
+    case POT_F32: return launch_backward_t<float>(bp, K, kGradAndColour, s);
+    case POT_F16: return launch_backward_t<__half>(bp, K, kGradAndColour, s);
+    default: return launch_backward_t<__nv_bfloat16>(bp, K, kGradAndColour, s);
     }
 }
 
