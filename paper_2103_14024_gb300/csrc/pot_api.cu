@@ -1132,23 +1132,24 @@ pot_status pot_render_backward_recorded(const pot_tree *t, int64_t n, const floa
                            reinterpret_cast<unsigned long long *>(const_cast<int64_t *>(seg_state))};
     // scratch of the bin order: bins of 2^bb leaves (count, start, cursor)
     // and the records' numbers in bin order
-    // POT_SEGBWD_ORDER (read once): 1 (default) visits the records in bin
-    // order, 0 in slot order (no scratch; faster when a batch's rays are
+    // POT_SEGBWD_ORDER (read once): 1 (default) visits the records in leaf
+    // order, 0 in slot order (no sort; as fast when a batch's rays are
     // already neighbours, e.g. whole pixel tiles)
     static const bool direct = [] {
         const char *e = std::getenv("POT_SEGBWD_ORDER");
         return e && std::atoi(e) == 0;
     }();
-    const int bb = segment_bin_log2(t->K);
-    if (bb < 0) return fail(POT_ERR_UNSUPPORTED, "SH degree not supported");
-    const int64_t nb = (t->n_leaves + (int64_t(1) << bb) - 1) >> bb;
+    // scratch of the leaf order: count, start, cursor per leaf, the scan's
+    // tile sums and the records' numbers in leaf order
+    const int64_t nl = t->n_leaves;
+    const int64_t n_tiles = (nl + kSegScanTile - 1) / kSegScanTile;
     Tmp bin_mem;
     SegmentBins bins{};
     if (!direct) {
-        POT_CUDA(bin_mem.alloc(sizeof(unsigned) * (size_t)(3 * nb + 1 + capacity), s), "alloc bins");
+        POT_CUDA(bin_mem.alloc(sizeof(unsigned) * (size_t)(3 * nl + 1 + n_tiles + capacity), s), "alloc sort");
         unsigned *base = static_cast<unsigned *>(bin_mem.p);
-        bins = SegmentBins{base, base + nb, base + 2 * nb + 1, base + 3 * nb + 1, nb};
-        POT_CUDA(cudaMemsetAsync(bins.count, 0, sizeof(unsigned) * (size_t)nb, s), "clear bins");
+        bins = SegmentBins{base, base + nl, base + 2 * nl + 1, base + 3 * nl + 1 + n_tiles, base + 3 * nl + 1, nl};
+        POT_CUDA(cudaMemsetAsync(bins.count, 0, sizeof(unsigned) * (size_t)nl, s), "clear counts");
     }
     POT_CUDA(launch_backward_recorded(p, t->n_leaves, sb, direct ? nullptr : &bins, grad_rgb, rgb_fwd, grad_sigma,
                                       grad_sh, t->desc.leaf_dtype, t->K, s),

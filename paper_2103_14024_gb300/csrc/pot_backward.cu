@@ -308,6 +308,25 @@ struct SegBackwardParams {
 #define POT_SEGBWD_MIN_BLOCKS 3
 #endif
 
+// The sum of v over the lanes of each run of adjacent lanes (run0: this
+// lane's run starts there), complete in the run's last lane (a scan within
+// runs).
+__device__ __forceinline__ float run_sum(float v, int lane, int run0)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane - d >= run0) v += t;
+    }
+    return v;
+}
+
+// Whole warps step over the records together.  Lanes next to each other
+// that hold records of the same leaf (records in leaf order, or neighbouring
+// rays of one forward step in slot order) form a run: the run's terms are
+// summed with shuffles and its last lane issues the float reductions, so a
+// leaf's row gets one set of reductions per warp and step instead of one per
+// record.
 template <int K, typename T>
 __global__ void __launch_bounds__(kBlock, POT_SEGBWD_MIN_BLOCKS) segment_backward_kernel(const SegBackwardParams q)
 {
@@ -315,39 +334,81 @@ __global__ void __launch_bounds__(kBlock, POT_SEGBWD_MIN_BLOCKS) segment_backwar
     const unsigned long long handed = q.sb.state[0];
     const int64_t used = q.perm ? (int64_t)*q.n_perm
                        : handed < (unsigned long long)q.sb.capacity ? (int64_t)handed : q.sb.capacity;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < used;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q.perm ? (int64_t)q.perm[k] : k;
-        const float4 a = __ldg(q.sb.rec + 2 * i);
-        const int ray = __float_as_int(a.x);
-        const int leaf = __float_as_int(a.y);
-        if (ray < 0 || ray >= q.n_rays) continue;  // an unused slot (ray -1)
-        if (leaf < 0 || leaf >= q.n_leaves) continue;
-        GradVisitor<K, T> gv;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gv.g[c] = __ldg(q.grad_rgb + 3 * (int64_t)ray + c);
-        if (gv.g[0] == 0.f && gv.g[1] == 0.f && gv.g[2] == 0.f) continue;
-        const float4 b = __ldg(q.sb.rec + 2 * i + 1);
-        gv.sig_arr = static_cast<const T *>(q.sigma);
-        gv.sh_arr = static_cast<const T *>(q.sh);
-        gv.gamma = 0.f;
-        gv.grad_sigma = q.grad_sigma;
-        gv.grad_sh = q.grad_sh;
-        gv.Tr = a.w;
-        gv.prefix[0] = b.x;
-        gv.prefix[1] = b.y;
-        gv.prefix[2] = b.z;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) gv.ctot[c] = __ldg(q.rgb_fwd + 3 * (int64_t)ray + c);
-        float d[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) d[r] = __ldg(q.ray_d + 3 * (int64_t)ray + r);
-        // the basis exactly as the walk computes it (Walker::begin)
-        const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
-        const float invlen = __frcp_rn(len);
+    const int lane = threadIdx.x & 31;
+    const T *sig_arr = static_cast<const T *>(q.sigma);
+    const T *sh_arr = static_cast<const T *>(q.sh);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); k0 < used; k0 += stride) {
+        const int64_t k = k0 + lane;
+        int leaf = -1;  // -1: no terms on this lane
+        float gx[3] = {0.f, 0.f, 0.f}, gsd = 0.f;
         RegY<K> Y;
-        sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y.v);
-        gv(leaf, a.z, Y);
+#pragma unroll
+        for (int j = 0; j < K; ++j) Y.v[j] = 0.f;
+        if (k < used) {
+            const int64_t i = q.perm ? (int64_t)q.perm[k] : k;
+            const float4 a = __ldg(q.sb.rec + 2 * i);
+            const int ray = __float_as_int(a.x), lf = __float_as_int(a.y);
+            // unused slots (ray -1) and records naming a ray or leaf out of range are skipped
+            if (ray >= 0 && ray < q.n_rays && lf >= 0 && lf < q.n_leaves) {
+                float g[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) g[c] = __ldg(q.grad_rgb + 3 * (int64_t)ray + c);
+                if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f) {
+                    const float4 b4 = __ldg(q.sb.rec + 2 * i + 1);
+                    float ctot[3], prefix[3] = {b4.x, b4.y, b4.z}, d[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) ctot[c] = __ldg(q.rgb_fwd + 3 * (int64_t)ray + c);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) d[c] = __ldg(q.ray_d + 3 * (int64_t)ray + c);
+                    // the basis exactly as the walk computes it (Walker::begin)
+                    const float len = sqrtf(fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2])));
+                    const float invlen = __frcp_rn(len);
+                    sh_basis<K>(d[0] * invlen, d[1] * invlen, d[2] * invlen, Y.v);
+                    float Tr = a.w;
+                    segment_terms<K, T>(sig_arr, sh_arr, lf, a.z, Y, g, ctot, prefix, Tr, gx, gsd);
+                    leaf = lf;
+                }
+            }
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, leaf, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || leaf != prev);
+        float *row = q.grad_sh + (int64_t)(leaf < 0 ? 0 : leaf) * (3 * K);
+        if (heads == 0xffffffffu) {  // no two adjacent lanes share a leaf: reductions per lane
+            if (leaf >= 0) {
+                if ((3 * K) % 4 == 0) {
+#pragma unroll
+                    for (int j = 0; j < 3 * K; j += 4)
+                        red_add4(row + j, gx[j % 3] * Y[j / 3], gx[(j + 1) % 3] * Y[(j + 1) / 3],
+                                 gx[(j + 2) % 3] * Y[(j + 2) / 3], gx[(j + 3) % 3] * Y[(j + 3) / 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 3 * K; ++j) red_add(row + j, gx[j % 3] * Y[j / 3]);
+                }
+                if (gsd != 0.f) red_add(q.grad_sigma + leaf, gsd);
+            }
+            continue;
+        }
+        const int run0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // last head at or before this lane
+        const bool tail = leaf >= 0 && (lane == 31 || ((heads >> (lane + 1)) & 1u));
+        if ((3 * K) % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < 3 * K; j += 4) {
+                const float v0 = run_sum(gx[j % 3] * Y[j / 3], lane, run0);
+                const float v1 = run_sum(gx[(j + 1) % 3] * Y[(j + 1) / 3], lane, run0);
+                const float v2 = run_sum(gx[(j + 2) % 3] * Y[(j + 2) / 3], lane, run0);
+                const float v3 = run_sum(gx[(j + 3) % 3] * Y[(j + 3) / 3], lane, run0);
+                if (tail) red_add4(row + j, v0, v1, v2, v3);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3 * K; ++j) {
+                const float v = run_sum(gx[j % 3] * Y[j / 3], lane, run0);
+                if (tail) red_add(row + j, v);
+            }
+        }
+        const float gs = run_sum(gsd, lane, run0);
+        if (tail && gs != 0.f) red_add(q.grad_sigma + leaf, gs);
     }
 }
 
@@ -374,43 +435,36 @@ cudaError_t launch_segment_backward_t(const SegBackwardParams &q, int K, cudaStr
     return cudaGetLastError();
 }
 
-// ---- recorded segments in bin order -----------------------------------------
-// The float reductions of the per-record kernel land on gradient rows spread
-// over all L leaves (L (1 + 3K) floats, far larger than L2).  Visiting the
-// records ordered by bin of 2^BB consecutive leaves (count, scan, scatter of
-// record numbers) makes neighbouring threads reduce into the same ~50 KB of
-// rows, which stay in L2.  (Summing each bin in shared memory and adding the
-// rows once, with no global atomics, measured slower: its blocks wait on
-// dependent loads between barriers.)
-
-// log2 of the leaves per bin: the largest 2^BB whose gradient rows,
-// (1 + 3K) floats each, fit in 64 KB.
-__host__ __device__ constexpr int bin_log2(int K)
-{
-    int b = 12;
-    while (b > 4 && (int64_t(1) << b) * (1 + 3 * K) * 4 > 65536) --b;
-    return b;
-}
+// ---- recorded segments in leaf order ----------------------------------------
+// The records are visited sorted by leaf (a counting sort: records per leaf,
+// a scan, the record numbers scattered to their leaf's range): a leaf's
+// records are then adjacent, so the per-record kernel merges them within a
+// warp, and neighbouring threads reduce into neighbouring gradient rows.
 
 struct SegBinParams {
     SegBackwardParams s;
-    const unsigned *start;  // [n_bins + 1] first sorted slot of each bin
-    unsigned *count;        // [n_bins] records per bin
+    const unsigned *start;  // [n_bins + 1] first sorted position of each leaf
+    unsigned *count;        // [n_bins] records per leaf
     unsigned *cursor;       // [n_bins] scatter cursors
-    unsigned *perm;         // [capacity] record numbers in bin order
-    int64_t n_bins;
+    unsigned *perm;         // [capacity] record numbers in leaf order
+    unsigned *tile_sum;     // [ceil(n_bins / kScanTile)] scan partials
+    int64_t n_bins;         // = n_leaves
 };
 
-// A record's bin, or -1 for an unused slot or one naming an out-of-range ray
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;  // counts per scan block
+static_assert(kScanTile == kSegScanTile, "scan tile of the scratch layout");
+
+// A record's leaf, or -1 for an unused slot or one naming an out-of-range ray
 // or leaf.
-template <int BB>
-__device__ __forceinline__ int record_bin(const SegBackwardParams &q, int64_t i, int64_t used)
+__device__ __forceinline__ int record_leaf(const SegBackwardParams &q, int64_t i, int64_t used)
 {
     if (i >= used) return -1;
     const float4 a = __ldg(q.sb.rec + 2 * i);
     const int ray = __float_as_int(a.x), leaf = __float_as_int(a.y);
     if (ray < 0 || ray >= q.n_rays || leaf < 0 || leaf >= q.n_leaves) return -1;
-    return leaf >> BB;
+    return leaf;
 }
 
 __device__ __forceinline__ int64_t records_used(const SegmentBuffer &sb)
@@ -419,12 +473,12 @@ __device__ __forceinline__ int64_t records_used(const SegmentBuffer &sb)
     return handed < (unsigned long long)sb.capacity ? (int64_t)handed : sb.capacity;
 }
 
-// Pass 1 (SCATTER = false): records per bin.  Pass 2 (SCATTER = true): each
-// record's number to its bin's part of perm.  Whole warps step together so
-// that lanes with the same bin (neighbouring rays of one step) share one
+// Pass 1 (SCATTER = false): records per leaf.  Pass 2 (SCATTER = true): each
+// record's number to its leaf's range of perm.  Whole warps step together so
+// that lanes with the same leaf (neighbouring rays of one step) share one
 // atomic, found with a match.
-template <int BB, bool SCATTER>
-__global__ void __launch_bounds__(kBlock) bin_pass_kernel(const SegBinParams q)
+template <bool SCATTER>
+__global__ void __launch_bounds__(kBlock) leaf_pass_kernel(const SegBinParams q)
 {
     if (q.s.sb.state[1] != 0ull) return;
     const int64_t used = records_used(q.s.sb);
@@ -432,7 +486,7 @@ __global__ void __launch_bounds__(kBlock) bin_pass_kernel(const SegBinParams q)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < used; i0 += stride) {
         const int64_t i = i0 + lane;
-        const int b = record_bin<BB>(q.s, i, used);
+        const int b = record_leaf(q.s, i, used);
         const unsigned m = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(m) - 1;
         if (!SCATTER) {
@@ -446,38 +500,91 @@ __global__ void __launch_bounds__(kBlock) bin_pass_kernel(const SegBinParams q)
     }
 }
 
-// Exclusive scan of the bin counts into start[0..n_bins] (one block) and
-// cleared cursors.
-__global__ void __launch_bounds__(1024) bin_scan_kernel(const SegBinParams q)
+// Exclusive scan of one value per thread over a block of kScanBlock threads;
+// *total = the block's sum.
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *total)
 {
-    __shared__ unsigned part[1024];
-    const int64_t nb = q.n_bins;
-    const int64_t per = (nb + 1023) / 1024;
-    const int64_t lo = threadIdx.x * per, hi = min(lo + per, nb);
-    unsigned sum = 0;
-    for (int64_t b = lo; b < hi; ++b) sum += q.count[b];
-    part[threadIdx.x] = sum;
+    __shared__ unsigned warp_sum[kScanBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (wid == 0) {
+        unsigned w = warp_sum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += t;
+        }
+        warp_sum[lane] = w;
     }
-    unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-    unsigned *start = const_cast<unsigned *>(q.start);
-    for (int64_t b = lo; b < hi; ++b) {
-        start[b] = run;
-        run += q.count[b];
-        q.cursor[b] = 0u;
-    }
-    if (threadIdx.x == 1023) start[nb] = part[1023];
+    __syncthreads();
+    *total = warp_sum[kScanBlock / 32 - 1];
+    return (wid ? warp_sum[wid - 1] : 0u) + incl - v;
 }
 
-template <int K, typename T>
-cudaError_t launch_binned_k(const SegBinParams &q, cudaStream_t s)
+// Scan step 1: the sum of each tile of kScanTile counts.
+__global__ void __launch_bounds__(kScanBlock) scan_tile_sums_kernel(const SegBinParams q)
 {
-    constexpr int BB = bin_log2(K);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned v = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u)
+        if (base + u < q.n_bins) v += q.count[base + u];
+    unsigned total;
+    block_exclusive_scan(v, &total);
+    if (threadIdx.x == 0) q.tile_sum[blockIdx.x] = total;
+}
+
+// Scan step 2 (one block): the tile sums become the tiles' exclusive offsets;
+// start[n_bins] = the number of records.
+__global__ void __launch_bounds__(kScanBlock) scan_tile_offsets_kernel(const SegBinParams q, int64_t n_tiles)
+{
+    const int64_t per = (n_tiles + kScanBlock - 1) / kScanBlock;
+    const int64_t lo = threadIdx.x * per, hi = min(lo + per, n_tiles);
+    unsigned v = 0;
+    for (int64_t t = lo; t < hi; ++t) v += q.tile_sum[t];
+    unsigned total;
+    unsigned run = block_exclusive_scan(v, &total);
+    for (int64_t t = lo; t < hi; ++t) {
+        const unsigned c = q.tile_sum[t];
+        q.tile_sum[t] = run;
+        run += c;
+    }
+    if (threadIdx.x == 0) const_cast<unsigned *>(q.start)[q.n_bins] = total;
+}
+
+// Scan step 3: each leaf's first sorted position; cursors cleared.
+__global__ void __launch_bounds__(kScanBlock) scan_apply_kernel(const SegBinParams q)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    unsigned c[kScanItems], v = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u) {
+        c[u] = base + u < q.n_bins ? q.count[base + u] : 0u;
+        v += c[u];
+    }
+    unsigned total;
+    unsigned run = block_exclusive_scan(v, &total) + q.tile_sum[blockIdx.x];
+    unsigned *start = const_cast<unsigned *>(q.start);
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u) {
+        if (base + u < q.n_bins) {
+            start[base + u] = run;
+            q.cursor[base + u] = 0u;
+        }
+        run += c[u];
+    }
+}
+
+template <typename T>
+cudaError_t launch_leaf_order_t(const SegBinParams &q, int K, cudaStream_t s)
+{
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -486,28 +593,18 @@ cudaError_t launch_binned_k(const SegBinParams &q, cudaStream_t s)
     int64_t blocks = (q.s.sb.capacity + kBlock - 1) / kBlock;
     if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
     if (blocks < 1) blocks = 1;
-    bin_pass_kernel<BB, false><<<(unsigned)blocks, kBlock, 0, s>>>(q);
-    bin_scan_kernel<<<1, 1024, 0, s>>>(q);
-    bin_pass_kernel<BB, true><<<(unsigned)blocks, kBlock, 0, s>>>(q);
-    count_launch(3);
-    // the per-record kernel over the records in bin order
+    const int64_t n_tiles = (q.n_bins + kScanTile - 1) / kScanTile;
+    leaf_pass_kernel<false><<<(unsigned)blocks, kBlock, 0, s>>>(q);
+    scan_tile_sums_kernel<<<(unsigned)n_tiles, kScanBlock, 0, s>>>(q);
+    scan_tile_offsets_kernel<<<1, kScanBlock, 0, s>>>(q, n_tiles);
+    scan_apply_kernel<<<(unsigned)n_tiles, kScanBlock, 0, s>>>(q);
+    leaf_pass_kernel<true><<<(unsigned)blocks, kBlock, 0, s>>>(q);
+    count_launch(5);
+    // the per-record kernel over the records in leaf order
     SegBackwardParams sq = q.s;
     sq.perm = q.perm;
     sq.n_perm = q.start + q.n_bins;
     return launch_segment_backward_t<T>(sq, K, s);
-}
-
-template <typename T>
-cudaError_t launch_binned_t(const SegBinParams &q, int K, cudaStream_t s)
-{
-    switch (K) {
-    case 1: return launch_binned_k<1, T>(q, s);
-    case 4: return launch_binned_k<4, T>(q, s);
-    case 9: return launch_binned_k<9, T>(q, s);
-    case 16: return launch_binned_k<16, T>(q, s);
-    case 25: return launch_binned_k<25, T>(q, s);
-    default: return cudaErrorInvalidValue;
-    }
 }
 
 // ---- optimiser step on the leaves ------------------------------------------
@@ -714,11 +811,6 @@ cudaError_t launch_mse_backward(const RenderParams &r, const float *target, floa
     }
 }
 
-int segment_bin_log2(int K)
-{
-    return (K == 1 || K == 4 || K == 9 || K == 16 || K == 25) ? bin_log2(K) : -1;
-}
-
 cudaError_t launch_backward_recorded(const RenderParams &r, int64_t n_leaves, const SegmentBuffer &sb,
                                      const SegmentBins *bins, const float *grad_rgb, const float *rgb_fwd,
                                      float *grad_sigma, float *grad_sh, int dtype, int K, cudaStream_t s)
@@ -727,11 +819,11 @@ cudaError_t launch_backward_recorded(const RenderParams &r, int64_t n_leaves, co
                         r.sh,    r.ray_d,    grad_rgb, rgb_fwd,    grad_sigma, grad_sh};
     cudaError_t e;
     if (bins) {
-        const SegBinParams bq{q, bins->start, bins->count, bins->cursor, bins->perm, bins->n_bins};
+        const SegBinParams bq{q, bins->start, bins->count, bins->cursor, bins->perm, bins->tile_sum, bins->n_bins};
         switch (dtype) {
-        case POT_F32: e = launch_binned_t<float>(bq, K, s); break;
-        case POT_F16: e = launch_binned_t<__half>(bq, K, s); break;
-        case POT_BF16: e = launch_binned_t<__nv_bfloat16>(bq, K, s); break;
+        case POT_F32: e = launch_leaf_order_t<float>(bq, K, s); break;
+        case POT_F16: e = launch_leaf_order_t<__half>(bq, K, s); break;
+        case POT_BF16: e = launch_leaf_order_t<__nv_bfloat16>(bq, K, s); break;
         default: return cudaErrorInvalidValue;
         }
     } else {

@@ -20,19 +20,20 @@ struct SegmentBuffer {
 // Forward of explicit rays (p.ray_o / p.ray_d, p.n_rays) that records its segments.
 cudaError_t launch_render_record(const RenderParams &p, const SegmentBuffer &sb, int dtype, int K, cudaStream_t s);
 
-// Scratch of the per-record backward in bin order: bins of
-// 2^segment_bin_log2(K) consecutive leaves; count zeroed by the caller.
+// Scratch of the per-record backward in leaf order (a counting sort of the
+// records by leaf); count zeroed by the caller.
+constexpr int kSegScanTile = 4096;  // counts per block of the scan
 struct SegmentBins {
-    unsigned *count;   // [n_bins]
-    unsigned *start;   // [n_bins + 1]
-    unsigned *cursor;  // [n_bins]
-    unsigned *perm;    // [capacity]
-    int64_t n_bins;
+    unsigned *count;     // [n_bins]
+    unsigned *start;     // [n_bins + 1]
+    unsigned *cursor;    // [n_bins]
+    unsigned *perm;      // [capacity]
+    unsigned *tile_sum;  // [ceil(n_bins / kSegScanTile)]
+    int64_t n_bins;      // = the tree's leaves
 };
-int segment_bin_log2(int K);
 
 // Gradients from the records, one thread per record with float reductions,
-// visiting the records in bin order (bins) or in slot order (null); then the walking
+// visiting the records in leaf order (bins) or in slot order (null); then the walking
 // backward over all rays, which runs only when the records overflowed (both
 // decide on the GPU).
 cudaError_t launch_backward_recorded(const RenderParams &r, int64_t n_leaves, const SegmentBuffer &sb,
