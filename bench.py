@@ -429,8 +429,8 @@ def train_measure(pot, torch, synth, scene, target_tree, args, barrier):
                              "bytes": "distinct leaves x (record + 2 x gradient row) + rays x 48 B; touched = "
                                       "segments x (record + gradient row) + rays x 48 B"},
             "bwd_launch": ("pot_render_mse_backward: colour walk + MSE + gradient walk" if args.train_fused
-                           else "pot_render_backward_recorded: one thread per segment recorded by the forward "
-                                "(pot_render_rays_record)" if records is not None
+                           else "pot_render_backward_recorded: the forward's recorded segments sorted by leaf, "
+                                "one thread per record, runs of a leaf merged in the warp" if records is not None
                            else "pot_render_backward with the forward colour given"),
             "record_ab": ab,
             "step_mrays_s": round(B / (ms * 1e-3) / 1e6, 2), "step_ms": round(ms, 4),

@@ -22,8 +22,9 @@
  * so pot_render_rays_record writes one record per composited segment and
  * pot_render_backward_recorded differentiates the records independently of
  * one another (one thread per record), without walking the rays again.  It
- * visits the records ordered by bin of consecutive leaves, so that the float
- * reductions of neighbouring threads meet the same gradient rows in L2.
+ * visits the records sorted by leaf: threads next to each other that hold
+ * records of the same leaf sum their terms first, and one of them adds the
+ * sum to the leaf's gradient row.
  *
  * Record buffer (caller-owned device memory):
  *   records   capacity x POT_SEGMENT_RECORD_BYTES bytes, 16-byte aligned.  A
@@ -70,12 +71,12 @@ pot_status pot_render_rays_record(const pot_tree *tree, int64_t n, const float *
  * dL/dC; rgb_fwd [n][3] is that call's colour output (background included).
  * origins / dirs are that call's rays (the directions give the SH basis; both
  * are used by the walking backward when the records overflowed).  All device
- * memory.  Launches on `stream`: the bin order of the records (count,
+ * memory.  Launches on `stream`: the sort of the records by leaf (count,
  * scan, scatter), the per-record kernel, then the walking backward; each
  * reads seg_state on the GPU and returns at once when the other one applies.
- * Scratch from the library's pool: 4 bytes per record slot plus 12 bytes per
- * bin (2^8 leaves at SH degree 3).  Float atomics make the summation order,
- * and so the last bits of the gradients, vary from call to call (as in
+ * Scratch from the library's pool: 4 bytes per record slot plus about 12
+ * bytes per leaf of the tree.  Float atomics make the summation order, and
+ * so the last bits of the gradients, vary from call to call (as in
  * pot_render_backward).                                                      */
 pot_status pot_render_backward_recorded(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
                                         const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
