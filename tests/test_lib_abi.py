@@ -82,3 +82,40 @@ def test_missing_library_fails_loudly(potlib, monkeypatch):
     monkeypatch.setattr(mod, "LIB_PATH", os.path.join(ROOT, "does-not-exist", "libpot.so"))
     with pytest.raises(RuntimeError):
         mod.lib()
+
+
+def test_segment_record_constants_match_header(potlib, tmp_path):
+    """The record size and slot block of include/pot_segments.h are the binding's,
+    and the binding's ctypes signatures of the two recorded-segment calls have
+    one argument per parameter of the header's declarations."""
+    prog = tmp_path / "seg.c"
+    prog.write_text("""
+#include <stdio.h>
+#include "pot_segments.h"
+int main(void) { printf("%d %d\\n", POT_SEGMENT_RECORD_BYTES, POT_SEGMENT_BLOCK); return 0; }
+""")
+    exe = tmp_path / "seg"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    rec, block = (int(v) for v in subprocess.check_output([str(exe)]).decode().split())
+    assert rec == potlib.SEGMENT_RECORD_BYTES == 32
+    assert block == potlib.SEGMENT_BLOCK
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "pot_segments.h")).read(), flags=re.S)
+    for name in ("pot_render_rays_record", "pot_render_backward_recorded"):
+        m = re.search(name + r"\s*\(([^)]*)\)", src)
+        assert m, name
+        n_params = len([p for p in m.group(1).split(",") if p.strip()])
+        assert len(potlib._SIGS[name]) == n_params, name
+
+
+def test_segment_records_buffer_host_logic(potlib):
+    """SegmentRecords sizing: 32-byte rows, a two-int64 state, and room for one
+    partly used block of slots per resident warp beyond the expected segments."""
+    import torch
+    r = potlib.SegmentRecords(1000, device="cpu")
+    assert r.records.shape == (1000, 8) and r.records.dtype == torch.float32
+    assert r.records.element_size() * r.records.shape[1] == potlib.SEGMENT_RECORD_BYTES
+    assert r.state.dtype == torch.int64 and r.state.tolist() == [0, 0]
+    assert potlib.SegmentRecords(0, device="cpu").records.shape[0] == 1   # never a zero-size tensor
+    big = potlib.SegmentRecords.for_rays(1 << 18, 64, device="cpu")
+    assert big.capacity >= (1 << 18) * 64 + 152 * 24 * potlib.SEGMENT_BLOCK   # 152 SMs x 24 resident warps
+    assert big.capacity < (1 << 31)
