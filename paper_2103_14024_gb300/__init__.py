@@ -599,19 +599,49 @@ def render_rays_diff(tree: Tree, sigma_param, sh_param, origins, dirs, bg=(0.0, 
                                float(far), records)
 
 
+def allreduce_leaf_grads(grad_sigma, grad_sh, op="mean", group=None):
+    """The exchange of data-parallel octree optimisation (Sec. 3.3 with the ray
+    batch split across ranks, the tree replicated on every rank): each rank
+    holds the leaf gradients of its part of the batch; after one all-reduce
+    per array every rank holds the gradient of the whole batch, so identical
+    optimiser steps keep the replicas equal.  ``op="mean"``: the ranks'
+    gradients are averaged, which is the gradient of the whole batch's mean
+    loss when every rank's loss is the mean over an equal share of the rays
+    (``pot_loss_mse``); ``op="sum"`` for summed losses.  In place; nothing to
+    do without an initialised process group of more than one rank."""
+    import torch.distributed as dist
+    if op not in ("mean", "sum"):
+        raise ValueError("op must be 'mean' or 'sum'")
+    if not dist.is_available() or not dist.is_initialized():
+        return
+    world = dist.get_world_size(group)
+    if world == 1:
+        return
+    for g in (grad_sigma, grad_sh):
+        dist.all_reduce(g, op=dist.ReduceOp.SUM, group=group)
+        if op == "mean":
+            g.div_(world)
+
+
 class LeafOptimizer:
-    """Owns the optimiser state of ``pot_step`` for one float32 tree."""
+    """Owns the optimiser state of ``pot_step`` for one float32 tree.  With
+    ``data_parallel=True`` (a process group initialised, one rank per GPU,
+    every rank holding the same tree) each step first averages the ranks'
+    gradients with ``allreduce_leaf_grads``."""
 
     def __init__(self, tree: Tree, kind="rmsprop", lr_sigma=1e-2, lr_sh=1e-2, alpha=0.99, beta1=0.9, beta2=0.999,
-                 eps=1e-8):
+                 eps=1e-8, data_parallel=False, group=None):
         import torch
         self.tree, self.kind = tree, kind
         self.hp = dict(lr_sigma=lr_sigma, lr_sh=lr_sh, alpha=alpha, beta1=beta1, beta2=beta2, eps=eps)
         nst = step_state_floats(tree, kind)
         self.state = torch.zeros(max(nst, 1), dtype=torch.float32, device="cuda")
         self.t = 0
+        self.data_parallel, self.group = data_parallel, group
 
     def step(self, grad_sigma, grad_sh, stream=None):
+        if self.data_parallel:
+            allreduce_leaf_grads(grad_sigma, grad_sh, "mean", self.group)
         self.t += 1
         step(self.tree, grad_sigma, grad_sh, self.state, self.kind, step_index=self.t, stream=stream, **self.hp)
 

@@ -124,3 +124,72 @@ def test_partitioned_render_equals_one_rank():
     assert joined.shape == whole.shape == (5, 16, 24, 3)
     assert np.array_equal(joined, whole)
     assert float(np.abs(whole).max()) > 0.0     # the views see the scene
+
+
+def _grad_worker(rank, world, port, out):
+    """One rank of data-parallel optimisation: the oracle's gradients of the
+    MSE (mean over this rank's rays) of its share of the batch, then the
+    library's all-reduce."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import paper_2103_14024_gb300 as pot
+    from oracle import oracle as O
+    from paper_2103_14024_gb300 import synth as S
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sc = S.scene_random(58, 4, 2, p_occ=0.35)
+    ot = O.build_sparse(sc)
+    o, d = S.random_rays(58, 600, radius=3.0, spread=0.9)
+    target = np.random.default_rng(58).uniform(size=(600, 3))
+    lo, hi = rank * 600 // world, (rank + 1) * 600 // world
+    col = O.render_rays(ot, o[lo:hi], d[lo:hi], near=0.2, far=8.0)["rgb"]
+    g = 2.0 * (col - target[lo:hi]) / (3 * (hi - lo))           # MSE over this rank's rays
+    gs, gh = O.backward_rays(ot, o[lo:hi], d[lo:hi], g, near=0.2, far=8.0)
+    gs_t = torch.from_numpy(gs.astype(np.float32))
+    gh_t = torch.from_numpy(gh.astype(np.float32))
+    pot.allreduce_leaf_grads(gs_t, gh_t, "mean")
+    out.put((rank, gs_t.numpy(), gh_t.numpy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_data_parallel_gradients_equal_one_rank(oracle_mod):
+    """Data-parallel optimisation (the ray batch split across 2 ranks, the tree
+    replicated): after the all-reduce every rank holds the gradient of the
+    whole batch's mean loss, the one-process gradient of all 600 rays."""
+    import numpy as np
+    import torch.multiprocessing as mp
+    from paper_2103_14024_gb300 import synth as S
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_grad_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(2)), key=lambda r: r[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    sc = S.scene_random(58, 4, 2, p_occ=0.35)
+    ot = oracle_mod.build_sparse(sc)
+    o, d = S.random_rays(58, 600, radius=3.0, spread=0.9)
+    target = np.random.default_rng(58).uniform(size=(600, 3))
+    col = oracle_mod.render_rays(ot, o, d, near=0.2, far=8.0)["rgb"]
+    rs, rh = oracle_mod.backward_rays(ot, o, d, 2.0 * (col - target) / (3 * 600), near=0.2, far=8.0)
+    for _, gs, gh in res:
+        assert np.abs(gs - rs).max() <= 1e-6 * np.abs(rs).max()
+        assert np.abs(gh - rh).max() <= 1e-6 * np.abs(rh).max()
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])   # replicas stay equal
+
+
+def test_allreduce_without_process_group_is_a_no_op():
+    import torch
+    sys.path.insert(0, ROOT)
+    import paper_2103_14024_gb300 as pot
+    a, b = torch.ones(3), torch.ones(2, 4)
+    pot.allreduce_leaf_grads(a, b)
+    assert a.tolist() == [1.0, 1.0, 1.0] and float(b.sum()) == 8.0
+    with pytest.raises(ValueError):
+        pot.allreduce_leaf_grads(a, b, op="max")
