@@ -37,10 +37,13 @@
  *   seg_state int64[2], device memory, written by the forward (it clears them
  *             first): [0] slots handed out, [1] nonzero when the records did
  *             not fit in `capacity` (the forward's colours are still exact).
- * Sizing: about (mean leaf segments per ray) x n + 256 x POT_SEGMENT_BLOCK
- * slots; when the records overflow, pot_render_backward_recorded detects it
- * on the GPU and computes the gradients by the walking backward instead
- * (same result, no host synchronisation).
+ * Sizing: about (mean leaf segments per ray) x n slots, plus one partly used
+ * block of POT_SEGMENT_BLOCK slots per resident warp of the recording kernel
+ * (3 blocks of 8 warps per SM: 3,648 warps on a 152-SM GB300); when the
+ * records overflow, pot_render_backward_recorded detects it on the GPU and
+ * computes the gradients by the walking backward instead (same result, no
+ * host synchronisation).  A buffer holds one forward's records: reuse it only
+ * after that forward's backward has been issued.
  */
 #ifndef POT_SEGMENTS_H
 #define POT_SEGMENTS_H

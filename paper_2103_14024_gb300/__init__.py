@@ -591,7 +591,8 @@ _RenderRaysFn = None
 def render_rays_diff(tree: Tree, sigma_param, sh_param, origins, dirs, bg=(0.0, 0.0, 0.0), gamma=0.0, near=0.0,
                      far=3.0e38, records: "SegmentRecords | None" = None):
     """Differentiable ``render_rays`` (torch.autograd.Function around pot_render_rays / pot_render_backward;
-    with ``records``, around pot_render_rays_record / pot_render_backward_recorded)."""
+    with ``records``, around pot_render_rays_record / pot_render_backward_recorded: the buffer keeps this
+    forward's records until its backward, so give each live forward its own buffer)."""
     global _RenderRaysFn
     if _RenderRaysFn is None:
         _RenderRaysFn = _autograd_fn()
