@@ -253,8 +253,10 @@ pot_status pot_render_rays(const pot_tree *tree, int64_t n, const float *origins
  * rgb_fwd is the forward colour C of each ray (pot_render_rays output, same
  * tree and opts); NULL makes the kernel recompute it in a first pass.
  * ACCUMULATES (+=) into grad_sigma [n_leaves] and grad_sh [n_leaves][K][3]
- * (float32, canonical layout); the caller zeroes them.  All arrays in device
- * memory.  Summation order of the float atomics is not deterministic.      */
+ * (float32, canonical layout); the caller zeroes them.  grad_sh must be
+ * 16-byte aligned when 3K is a multiple of 4 (rows are added in 16-byte
+ * vectors), else POT_ERR_INVALID_ARG.  All arrays in device memory.
+ * Summation order of the float atomics is not deterministic.               */
 pot_status pot_render_backward(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
                                const float *grad_rgb, const float *rgb_fwd, const pot_render_opts *opts,
                                float *grad_sigma, float *grad_sh, pot_stream stream);
@@ -267,8 +269,9 @@ pot_status pot_render_backward(const pot_tree *tree, int64_t n, const float *ori
  * ACCUMULATED into grad_sigma [n_leaves] and grad_sh [n_leaves][K][3].  rgb
  * [n][3] receives C when not NULL.  Each ray is walked twice in the same
  * launch (colour, then gradients), so no colour buffer or second launch is
- * needed.  target [n][3] float32; every array in device memory.  Float atomic
- * summation order (gradients, loss) is not deterministic.                  */
+ * needed.  target [n][3] float32; every array in device memory; grad_sh
+ * aligned as for pot_render_backward.  Float atomic summation order
+ * (gradients, loss) is not deterministic.                                  */
 pot_status pot_render_mse_backward(const pot_tree *tree, int64_t n, const float *origins, const float *dirs,
                                    const float *target, const pot_render_opts *opts, float *rgb, float *loss,
                                    float *grad_sigma, float *grad_sh, pot_stream stream);

@@ -70,7 +70,8 @@ pot_status pot_render_rays_record(const pot_tree *tree, int64_t n, const float *
 /* The gradients of pot_render_backward (App. B.3.2) from the records of the
  * pot_render_rays_record call that rendered the same rays with the same
  * tree values and opts: accumulates (+=) dL/dsigma into grad_sigma [L] and
- * dL/dk into grad_sh [L][K][3] (float32, caller-zeroed).  grad_rgb [n][3] is
+ * dL/dk into grad_sh [L][K][3] (float32, caller-zeroed; 16-byte aligned when
+ * 3K is a multiple of 4, else POT_ERR_INVALID_ARG).  grad_rgb [n][3] is
  * dL/dC; rgb_fwd [n][3] is that call's colour output (background included).
  * origins / dirs are that call's rays (the directions give the SH basis; both
  * are used by the walking backward when the records overflowed).  All device

@@ -336,6 +336,13 @@ pot_status check_opts(const pot_render_opts *o)
     return POT_OK;
 }
 
+// The gradient kernels add whole 16-byte vectors to grad_sh rows when a row
+// (3K floats) is a multiple of 4 floats.
+bool grad_sh_aligned(const pot_tree *t, const float *grad_sh)
+{
+    return (3 * t->K) % 4 != 0 || ((uintptr_t)grad_sh & 15u) == 0;
+}
+
 void fill_tree_params(RenderParams &p, const pot_tree *t, const pot_render_opts *o)
 {
     std::memset(&p, 0, sizeof(p));
@@ -972,6 +979,7 @@ pot_status pot_render_backward(const pot_tree *t, int64_t n, const float *origin
     if (st != POT_OK) return st;
     if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
     if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    if (!grad_sh_aligned(t, grad_sh)) return fail(POT_ERR_INVALID_ARG, "grad_sh must be 16-byte aligned");
     const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
     if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
     DeviceGuard g(t->device);
@@ -1011,6 +1019,7 @@ pot_status pot_render_mse_backward(const pot_tree *t, int64_t n, const float *or
     if (st != POT_OK) return st;
     if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
     if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    if (leaves && !grad_sh_aligned(t, grad_sh)) return fail(POT_ERR_INVALID_ARG, "grad_sh must be 16-byte aligned");
     const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
     if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
     DeviceGuard g(t->device);
@@ -1111,6 +1120,7 @@ pot_status pot_render_backward_recorded(const pot_tree *t, int64_t n, const floa
     if (st != POT_OK) return st;
     if (opts && opts->seg_count) return fail(POT_ERR_INVALID_ARG, "counting outputs are not used by the backward");
     if (t->desc.leaf_dtype == POT_CB16) return fail(POT_ERR_UNSUPPORTED, "no gradients for codebook leaves");
+    if (!grad_sh_aligned(t, grad_sh)) return fail(POT_ERR_INVALID_ARG, "grad_sh must be 16-byte aligned");
     const float near = opts ? opts->near : 0.f, far = opts ? opts->far : 3.0e38f;
     if (!(near >= 0.f) || std::isnan(far)) return fail(POT_ERR_INVALID_ARG, "bad near / far");
     DeviceGuard g(t->device);

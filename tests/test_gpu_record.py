@@ -270,6 +270,19 @@ def test_record_argument_checks(pot, torch_mod):
     st = L.pot_render_backward_recorded(t.handle, 64, P(og), P(od), P(gg), P(o), C.byref(opts), P(recs.records),
                                         recs.capacity, P(recs.state), P(gs), P(gh), pot._stream())
     assert st == 1                                                # host rgb_fwd
+    # grad_sh rows are added in 16-byte vectors (3K = 12 floats here): a
+    # misaligned gradient array is refused by every backward before any launch
+    t3 = pot.Tree.from_scene(S.scene_random(99, 4, 1, p_occ=0.35))
+    gh_buf = torch.zeros(t3.info()["n_leaves"] * 12 + 4, device="cuda")
+    bad = C.c_void_p(gh_buf.data_ptr() + 4)
+    st = L.pot_render_backward_recorded(t3.handle, 64, P(og), P(od), P(gg), P(rgb), C.byref(opts), P(recs.records),
+                                        recs.capacity, P(recs.state), P(gs), bad, pot._stream())
+    assert st == 1
+    assert L.pot_render_backward(t3.handle, 64, P(og), P(od), P(gg), P(rgb), C.byref(opts), P(gs), bad,
+                                 pot._stream()) == 1
+    loss = torch.zeros(1, device="cuda")
+    assert L.pot_render_mse_backward(t3.handle, 64, P(og), P(od), P(gg), C.byref(opts), None, P(loss), P(gs), bad,
+                                     pot._stream()) == 1
     recs.state.fill_(7)
     assert L.pot_render_rays_record(t.handle, 0, None, None, C.byref(opts), None, None, P(recs.records),
                                     recs.capacity, P(recs.state), pot._stream()) == pot.POT_OK
