@@ -216,6 +216,56 @@ def test_backward_recorded_main_depth5(pot, torch_mod, gamma):
     pot.check()
 
 
+@pytest.mark.parametrize("cells", ["none", "brick"])
+def test_record_path_without_dense_index(pot, torch_mod, cells):
+    """The recording forward and the recorded backward on a tree located by
+    the child-array descent (no cell index: the walker's ancestor stack in
+    dynamic shared memory) and by the brick layout of the index: colours
+    bit-identical to pot_render_rays, gradients equal to the walking
+    backward's."""
+    torch = torch_mod
+    sc = S.scene_random(88, 6, 3, p_occ=0.35, sigma_mu=1.5, sigma_s=1.0, sh_std=0.8)
+    t = pot.Tree.from_scene(sc)
+    t.set_cell_index(cells)
+    o, d = S.random_rays(88, 3001, radius=3.0, spread=0.9)
+    g = np.random.default_rng(88).normal(size=(o.shape[0], 3)).astype(np.float32)
+    og, od, gg = (torch.from_numpy(a).cuda() for a in (o, d, g))
+    ref = pot.render_rays(t, og, od, gamma=1e-3, near=0.2, far=8.0)
+    recs = pot.SegmentRecords.for_rays(o.shape[0], 32)
+    rgb = pot.render_rays_record(t, og, od, recs, gamma=1e-3, near=0.2, far=8.0)
+    assert torch.equal(rgb, ref) and not recs.overflowed()
+    gs, gh = pot.render_backward_recorded(t, og, od, gg, rgb, recs, gamma=1e-3, near=0.2, far=8.0)
+    ws, wh = pot.render_backward(t, og, od, gg, rgb_fwd=rgb, gamma=1e-3, near=0.2, far=8.0)
+    assert float(ws.abs().max()) > 0
+    _close(gs.cpu().numpy(), ws.cpu().numpy(), f"grad_sigma vs walking ({cells})", rel=1e-5)
+    _close(gh.cpu().numpy(), wh.cpu().numpy(), f"grad_sh vs walking ({cells})", rel=1e-5)
+    pot.check()
+
+
+def test_record_path_empty_tree_and_misses(pot, torch_mod):
+    """An empty tree: background colours, no records, zero gradients; rays
+    that miss a non-empty tree add no records either."""
+    torch = torch_mod
+    sc = S.scene_random(89, 4, 1, p_occ=0.35)
+    empty = sc.replace(morton=sc.morton[:0], sigma=sc.sigma[:0], sh=sc.sh[:0])
+    te = pot.Tree.from_scene(empty)
+    o, d = S.random_rays(89, 500, radius=3.0, spread=0.9)
+    og, od = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    recs = pot.SegmentRecords.for_rays(500, 8)
+    bg = (0.25, 0.5, 0.75)
+    rgb = pot.render_rays_record(te, og, od, recs, bg=bg, near=0.2, far=8.0)
+    assert torch.equal(rgb, torch.tensor(bg, device="cuda").expand(500, 3))
+    assert recs.used() == 0 and not recs.overflowed()
+    gs, gh = pot.render_backward_recorded(te, og, od, torch.ones_like(rgb), rgb, recs, bg=bg, near=0.2, far=8.0)
+    assert gs.numel() == 0 and gh.numel() == 0
+    t = pot.Tree.from_scene(sc)
+    away = torch.tensor([[0.0, 0.0, 1.0]], device="cuda").expand(500, 3).contiguous()
+    orig = torch.tensor([[0.0, 0.0, 5.0]], device="cuda").expand(500, 3).contiguous()   # pointing away
+    pot.render_rays_record(t, orig, away, recs, near=0.0, far=8.0)
+    assert recs.used() == 0
+    pot.check()
+
+
 def test_recorded_autograd(pot, torch_mod):
     """render_rays_diff with records: the gradients of the walking autograd path."""
     torch = torch_mod
