@@ -539,6 +539,26 @@ def serve_measure(pot, torch, synth, args):
     return out
 
 
+def pinned_d2h_gbs(torch, host):
+    """Copy rate (GB/s) from device memory into the pinned host buffer ``host``
+    (one warm-up copy, then one timed with CUDA events); None if it cannot be
+    measured."""
+    try:
+        dev = torch.empty(host.shape, dtype=host.dtype, device="cuda")
+        host.copy_(dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        host.copy_(dev, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        nbytes = host.numel() * host.element_size()
+        del dev
+        return round(nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1)
+    except Exception:  # noqa: BLE001
+        return None
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     """W untimed steps, then K steps bracketed by barrier + synchronize; returns (host wall
     seconds, per-step CUDA-event ms, CUDA-event seconds from the first step's start to the
@@ -689,6 +709,7 @@ def main():
             ke = max(5, args.steps // 2)
             wall_e, _, _ = time_steps(torch, step_e2e, ke, 2, barrier)   # host wall clock: end to end
             res["e2e_wall"] = wall_e / ke
+            res["d2h_gbs"] = pinned_d2h_gbs(torch, host)
             del host
         return res
 
@@ -751,7 +772,10 @@ def main():
         e2e_value = job_rays / e2e_wall / 1e6
         n_job_views = job_rays // (W * H)
         line["e2e"] = {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": 80 * n_job_views,
-                       "d2h_bytes_per_step": 12 * job_rays}
+                       "d2h_bytes_per_step": 12 * job_rays,
+                       "pinned_d2h_gbs": main_res.get("d2h_gbs"),
+                       "d2h_note": "device-to-pinned-host copy rate of this box for an image-sized buffer "
+                                   "(one copy, CUDA events); the end-to-end number follows it"}
     variants = {}
     # per-GPU characteristics (other leaf types, training, serving) are measured at N = 1 only
     extras = world == 1
