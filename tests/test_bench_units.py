@@ -42,3 +42,12 @@ def test_kernel_sha_covers_the_render_sources():
     assert len(sha) == 16 and all(c in "0123456789abcdef" for c in sha)
     for f in bench.KERNEL_SOURCES:
         assert os.path.exists(os.path.join(ROOT, "paper_2103_14024_gb300", f))
+
+
+def test_pinned_d2h_rate_is_none_without_a_gpu():
+    """The copy-rate figure beside the end-to-end number is measured, never
+    guessed: without a CUDA device it is None."""
+    import torch
+    if torch.cuda.is_available():
+        return
+    assert bench.pinned_d2h_gbs(torch, torch.empty(16)) is None
