@@ -293,6 +293,50 @@ def test_camera_ray_fp32_expression(oracle_mod):
         k += W * H
 
 
+def test_camera_rays_project_back_to_their_pixels(oracle_mod):
+    """Pinhole geometry of the camera rays (reading R2: looks along its -z
+    axis, image rows grow downwards): a point on the ray of pixel (i, j),
+    taken into the camera frame with the inverse of the camera's rotation and
+    projected with the focal lengths and principal point, lands on the pixel
+    centre (i + 0.5, j + 0.5); the ray of the principal point is the camera's
+    -z axis; the orbit cameras' central rays pass through the origin."""
+    for cams in (S.cameras_tiny("generic"), S.cameras_main(3), S.cameras_train(n=3)):
+        o, d = oracle_mod.cam_rays(cams)
+        k = 0
+        for c in cams:
+            W, H = int(c["width"]), int(c["height"])
+            M = c["c2w"].astype(np.float64)
+            R, ctr = M[:, :3], M[:, 3]
+            assert np.allclose(R.T @ R, np.eye(3), atol=1e-6)           # a rotation
+            j, i = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+            oo, dd = o[k:k + W * H].astype(np.float64), d[k:k + W * H].astype(np.float64)
+            assert np.allclose(oo, ctr)
+            q = (dd * 3.0) @ R                                            # R^T (p - centre), p = o + 3 d
+            u = c["cx"] + c["fx"] * q[:, 0] / -q[:, 2]
+            v = c["cy"] - c["fy"] * q[:, 1] / -q[:, 2]
+            assert np.all(q[:, 2] < 0)                                    # in front of the camera
+            assert np.abs(u - (i.ravel() + 0.5)).max() < 1e-3
+            assert np.abs(v - (j.ravel() + 0.5)).max() < 1e-3
+            k += W * H
+        # the ray through the principal point is the -z axis of the camera
+        c = cams[0]
+        cam1 = c.copy()
+        cam1["cx"], cam1["cy"] = 0.5, 0.5                                 # pixel (0, 0) at the principal point
+        _, d0 = oracle_mod.cam_rays(np.array([cam1]))
+        assert np.allclose(d0[0], -c["c2w"][:, 2], atol=1e-7)
+    # orbit cameras look at the origin: the central pixel's ray passes it closely
+    for cams in (S.cameras_main(4), S.cameras_train(n=4)):
+        o, d = oracle_mod.cam_rays(cams)
+        n = int(cams[0]["width"]) * int(cams[0]["height"])
+        for v_ in range(len(cams)):
+            W, H = int(cams[v_]["width"]), int(cams[v_]["height"])
+            r = v_ * n + (H // 2) * W + W // 2
+            oo, dd = o[r].astype(np.float64), d[r].astype(np.float64)
+            dd /= np.linalg.norm(dd)
+            miss = np.linalg.norm(np.cross(-oo, dd))                      # distance of the origin from the ray
+            assert miss < 4.0 / min(float(cams[v_]["fx"]), float(cams[v_]["fy"])) * 1.5
+
+
 def test_render_cams_equals_render_rays(oracle_mod):
     sc = S.scene_tiny()
     t = oracle_mod.build_sparse(sc)
